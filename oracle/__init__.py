@@ -1,0 +1,222 @@
+"""CPU oracle for the track-finding path -- TEST INFRASTRUCTURE ONLY.
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg may import this package.  The product path (the CUDA library and its
+Python binding) never calls it and never falls back to it.
+
+This is a ctypes binding over ``hough_oracle.c`` (plain single-threaded C, see
+the header comment there for what it computes and which passage of the paper
+each step follows).  The shared object is compiled with gcc on first use.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hough_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+PEAK_DTYPE = np.dtype([("theta", "<u2"), ("rho", "<u2"), ("votes", "<i4"),
+                       ("n_hits", "<i4"), ("hit_begin", "<i4")])
+
+WIN_PEAK_OVERFLOW = 1
+WIN_HIT_OUT_OF_RANGE = 2
+WIN_VOTE_OUT_OF_RANGE = 4
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("n_vanes", ctypes.c_int32), ("n_z_strips", ctypes.c_int32),
+                ("z_pitch_u", ctypes.c_int32), ("z_min_u", ctypes.c_int32),
+                ("phi_u_per_deg", ctypes.c_int32), ("z_u_per_mm", ctypes.c_int32),
+                ("rho_min", ctypes.c_double), ("rho_max", ctypes.c_double)]
+
+
+class Thresholds(ctypes.Structure):
+    _fields_ = [("vote_threshold", ctypes.c_int32), ("assoc_tol_bins", ctypes.c_int32),
+                ("max_peaks", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+def build(force: bool = False) -> str:
+    """Compile hough_oracle.c into a shared object (gcc, -O2, no -march)."""
+    with _lock:
+        if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+            os.makedirs(_BUILD, exist_ok=True)
+            tmp = _SO + f".{os.getpid()}.tmp"
+            subprocess.run(["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared",
+                            "-o", tmp, _SRC, "-lm"], check=True)
+            os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        i64 = ctypes.c_int64
+        i32 = ctypes.c_int
+        lib.oracle_tables.argtypes = [P, i32, i32, P, P, P]
+        lib.oracle_tables.restype = i32
+        lib.oracle_encode.argtypes = [P, P, P, i64, P, P]
+        lib.oracle_encode.restype = None
+        lib.oracle_vote.argtypes = [P, i32, i32, P, P, i64, P]
+        lib.oracle_vote.restype = i64
+        lib.oracle_bins_fp64.argtypes = [P, i32, i32, P, P, i64, P]
+        lib.oracle_bins_fp64.restype = None
+        lib.oracle_bins_fixed.argtypes = [P, i32, i32, P, P, i64, P]
+        lib.oracle_bins_fixed.restype = None
+        lib.oracle_peaks.argtypes = [P, i32, i32, ctypes.c_int32, ctypes.c_int32, P, P]
+        lib.oracle_peaks.restype = ctypes.c_int32
+        lib.oracle_find_window.argtypes = [P, i32, i32, P, P, P, i64, P, P, P, P, P, P, P, P]
+        lib.oracle_find_window.restype = i32
+        lib.oracle_find_batch.argtypes = [P, i32, i32, P, P, P, P, i64, P, P, P, P, P, P, P]
+        lib.oracle_find_batch.restype = i32
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def make_geometry(d: dict) -> Geometry:
+    return Geometry(d["n_vanes"], d["n_z_strips"], d["z_pitch_u"], d["z_min_u"],
+                    d["phi_u_per_deg"], d["z_u_per_mm"], float(d["rho_min"]), float(d["rho_max"]))
+
+
+def make_thresholds(vote_threshold=5, assoc_tol_bins=1, max_peaks=64, flags=0) -> Thresholds:
+    return Thresholds(vote_threshold, assoc_tol_bins, max_peaks, flags)
+
+
+def tables(geom: dict, n_theta: int, n_rho: int):
+    """(C int32[n_theta], S int32[n_theta], D int) fixed-point tables."""
+    lib = _load()
+    g = make_geometry(geom)
+    C = np.zeros(n_theta, np.int32)
+    S = np.zeros(n_theta, np.int32)
+    D = np.zeros(1, np.int64)
+    rc = lib.oracle_tables(ctypes.byref(g), n_theta, n_rho, _ptr(C), _ptr(S), _ptr(D))
+    if rc != 0:
+        raise ValueError("bad geometry or shape")
+    return C, S, int(D[0])
+
+
+def encode(geom: dict, vane, strip):
+    lib = _load()
+    g = make_geometry(geom)
+    vane = np.ascontiguousarray(vane, np.int32)
+    strip = np.ascontiguousarray(strip, np.int32)
+    phi = np.zeros(len(vane), np.int32)
+    z = np.zeros(len(vane), np.int32)
+    lib.oracle_encode(ctypes.byref(g), _ptr(vane), _ptr(strip), len(vane), _ptr(phi), _ptr(z))
+    return phi, z
+
+
+def vote(geom: dict, n_theta: int, n_rho: int, phi_q, z_q):
+    """(acc int32[n_theta, n_rho], n_dropped)."""
+    lib = _load()
+    g = make_geometry(geom)
+    phi_q = np.ascontiguousarray(phi_q, np.int32)
+    z_q = np.ascontiguousarray(z_q, np.int32)
+    acc = np.zeros((n_theta, n_rho), np.int32)
+    dropped = lib.oracle_vote(ctypes.byref(g), n_theta, n_rho, _ptr(phi_q), _ptr(z_q),
+                              len(phi_q), _ptr(acc))
+    return acc, int(dropped)
+
+
+def bins_fixed(geom: dict, n_theta: int, n_rho: int, phi_q, z_q):
+    lib = _load()
+    g = make_geometry(geom)
+    phi_q = np.ascontiguousarray(phi_q, np.int32)
+    z_q = np.ascontiguousarray(z_q, np.int32)
+    out = np.zeros((len(phi_q), n_theta), np.int64)
+    lib.oracle_bins_fixed(ctypes.byref(g), n_theta, n_rho, _ptr(phi_q), _ptr(z_q), len(phi_q),
+                          _ptr(out))
+    return out
+
+
+def bins_fp64(geom: dict, n_theta: int, n_rho: int, phi_q, z_q):
+    lib = _load()
+    g = make_geometry(geom)
+    phi_q = np.ascontiguousarray(phi_q, np.int32)
+    z_q = np.ascontiguousarray(z_q, np.int32)
+    out = np.zeros((len(phi_q), n_theta), np.int64)
+    lib.oracle_bins_fp64(ctypes.byref(g), n_theta, n_rho, _ptr(phi_q), _ptr(z_q), len(phi_q),
+                         _ptr(out))
+    return out
+
+
+def peaks(acc, threshold: int, max_peaks: int):
+    """Peaks of a given accumulator: (peaks[n_kept] structured, n_found)."""
+    lib = _load()
+    acc = np.ascontiguousarray(acc, np.int32)
+    n_theta, n_rho = acc.shape
+    out = np.zeros(max(max_peaks, 1), PEAK_DTYPE)
+    kept = np.zeros(1, np.int32)
+    found = lib.oracle_peaks(_ptr(acc), n_theta, n_rho, threshold, max_peaks, _ptr(out),
+                             _ptr(kept))
+    return out[: int(kept[0])].copy(), int(found)
+
+
+def find_window(geom: dict, n_theta: int, n_rho: int, phi_q, z_q, vote_threshold=5,
+                assoc_tol_bins=1, max_peaks=64):
+    """One window through voting, peaks and association; returns a dict."""
+    lib = _load()
+    g = make_geometry(geom)
+    th = make_thresholds(vote_threshold, assoc_tol_bins, max_peaks)
+    phi_q = np.ascontiguousarray(phi_q, np.int32)
+    z_q = np.ascontiguousarray(z_q, np.int32)
+    n = len(phi_q)
+    acc = np.zeros((n_theta, n_rho), np.int32)
+    dropped = np.zeros(1, np.int64)
+    pk = np.zeros(max(max_peaks, 1), PEAK_DTYPE)
+    n_peaks = np.zeros(1, np.int32)
+    n_found = np.zeros(1, np.int32)
+    hit_track = np.zeros(n, np.int32)
+    track_hits = np.zeros(n, np.int32)
+    status = np.zeros(1, np.uint32)
+    rc = lib.oracle_find_window(ctypes.byref(g), n_theta, n_rho, ctypes.byref(th), _ptr(phi_q),
+                                _ptr(z_q), n, _ptr(acc), _ptr(dropped), _ptr(pk), _ptr(n_peaks),
+                                _ptr(n_found), _ptr(hit_track), _ptr(track_hits), _ptr(status))
+    if rc != 0:
+        raise ValueError("oracle_find_window: bad arguments")
+    k = int(n_peaks[0])
+    return dict(acc=acc, n_dropped=int(dropped[0]), peaks=pk[:k].copy(), n_peaks=k,
+                n_found=int(n_found[0]), hit_track=hit_track, track_hits=track_hits,
+                status=int(status[0]))
+
+
+def find_batch(geom: dict, n_theta: int, n_rho: int, phi_q, z_q, offsets, vote_threshold=5,
+               assoc_tol_bins=1, max_peaks=64, export_acc=False):
+    """A CSR batch of windows; outputs in the library's layout (dict of arrays)."""
+    lib = _load()
+    g = make_geometry(geom)
+    th = make_thresholds(vote_threshold, assoc_tol_bins, max_peaks)
+    phi_q = np.ascontiguousarray(phi_q, np.int32)
+    z_q = np.ascontiguousarray(z_q, np.int32)
+    offsets = np.ascontiguousarray(offsets, np.int64)
+    nw = len(offsets) - 1
+    n = len(phi_q)
+    acc = np.zeros((nw, n_theta, n_rho), np.int32) if export_acc else None
+    pk = np.zeros(nw * max(max_peaks, 0), PEAK_DTYPE)
+    n_peaks = np.zeros(nw, np.int32)
+    n_found = np.zeros(nw, np.int32)
+    hit_track = np.zeros(n, np.int32)
+    track_hits = np.zeros(n, np.int32)
+    status = np.zeros(nw, np.uint32)
+    rc = lib.oracle_find_batch(ctypes.byref(g), n_theta, n_rho, ctypes.byref(th), _ptr(phi_q),
+                               _ptr(z_q), _ptr(offsets), nw, _ptr(acc), _ptr(pk), _ptr(n_peaks),
+                               _ptr(n_found), _ptr(hit_track), _ptr(track_hits), _ptr(status))
+    if rc != 0:
+        raise ValueError("oracle_find_batch: bad arguments")
+    return dict(acc=acc, peaks=pk.reshape(nw, max_peaks) if max_peaks else pk.reshape(nw, 0),
+                n_peaks=n_peaks, n_found=n_found, hit_track=hit_track, track_hits=track_hits,
+                status=status)

@@ -1,0 +1,423 @@
+/*
+ * hough_oracle.c -- plain, slow, single-threaded CPU oracle for the
+ * track-finding hot path (Hough voting -> peak extraction -> association).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * execute this file; only the tests, the smoke check and the benchmark's CPU
+ * baseline leg use it.  It shares no code, header, table or constant generator
+ * with the CUDA library: every step below is written out independently from
+ * the paper's definitions, in the most direct form (full int32 accumulator,
+ * double loops, explicit floor division, qsort).
+ *
+ * What it computes, per time window (Section 4 Eq. (1); Section 5):
+ *   A. encoding: a RecoHit on vane k, z-strip j has phi = 9 deg * k (radial
+ *      vanes, Section 2) and z at the centre of strip j, both in fixed-point
+ *      units of 1/200 degree and 1/200 mm;
+ *   B. Hough voting: every hit votes once in each theta row t for the rho bin
+ *      b = floor((phi*C[t] + z*S[t] + D) / 2^24); votes outside [0, n_rho)
+ *      are dropped and counted (Section 4 Eq. (1); Section 5 binning);
+ *   C. peaks: every bin with count >= T that is a 3x3 local maximum under the
+ *      row-major tie-break, sorted by (votes desc, theta asc, rho asc), the
+ *      first max_peaks kept (Section 4 and Section 5, "the bin with the highest
+ *      number of entries", generalised to pileup);
+ *   D. association: each hit goes to the first peak in that order whose line
+ *      it lies on within the tolerance, |b_h(t_p) - b_p| <= tol (Section 5,
+ *      seed hits "that align with the straight line"); then the hits are
+ *      grouped per peak.
+ * The readings of the points the paper leaves open (units, theta sampling,
+ * fixed-point tables, threshold, tie-break, tolerance) are listed in the
+ * design notes of the repository.
+ *
+ * Parity pins: tests/test_oracle_pins.py checks this file against brute force
+ * on hand-built cases, the single-line closed form, the helix closed form,
+ * the FP64 continuous definition (|b_fixed - b_fp64| <= 1), conservation of
+ * votes and permutation invariance.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_FRAC_BITS 24
+
+/* Same field order as the library's geometry struct; declared here on its own. */
+typedef struct {
+    int32_t n_vanes;
+    int32_t n_z_strips;
+    int32_t z_pitch_u;
+    int32_t z_min_u;
+    int32_t phi_u_per_deg;
+    int32_t z_u_per_mm;
+    double rho_min;
+    double rho_max;
+} oracle_geometry;
+
+typedef struct {
+    int32_t vote_threshold;
+    int32_t assoc_tol_bins;
+    int32_t max_peaks;
+    uint32_t flags;
+} oracle_thresholds;
+
+typedef struct {
+    uint16_t theta;
+    uint16_t rho;
+    int32_t votes;
+    int32_t n_hits;
+    int32_t hit_begin;
+} oracle_peak;
+
+enum {
+    ORACLE_WIN_PEAK_OVERFLOW = 1u,
+    ORACLE_WIN_HIT_OUT_OF_RANGE = 2u,
+    ORACLE_WIN_VOTE_OUT_OF_RANGE = 4u,
+};
+
+/* ---------------------------------------------------------------- helpers */
+
+/* Round half away from zero, on a double. */
+static int64_t round_half_away(double x)
+{
+    if (x >= 0.0)
+        return (int64_t)floor(x + 0.5);
+    return -(int64_t)floor(-x + 0.5);
+}
+
+/* Floor division by a positive divisor, written out with / and %. */
+static int64_t floor_div(int64_t num, int64_t den)
+{
+    int64_t q = num / den;
+    int64_t r = num % den;
+    if (r != 0 && num < 0)
+        q -= 1;
+    return q;
+}
+
+/* --------------------------------------------------------------- step A/B */
+
+/*
+ * Fixed-point cos/sin tables (Section 4 Eq. (1) with the Section 5 binning).
+ * theta_t = (t + 1/2) * pi / n_theta (bin centres over 0..180 degrees).
+ * One rho bin is (rho_max - rho_min)/n_rho; a hit's rho in bins, measured
+ * from rho_min, is (phi/u_phi*cos + z/u_z*sin - rho_min) * n_rho/(rho_max - rho_min).
+ * The tables hold those factors scaled by 2^24 and rounded half away from zero:
+ *   C[t] = round(cos(theta_t) * 2^24 * n_rho / ((rho_max - rho_min) * u_phi))
+ *   S[t] = round(sin(theta_t) * 2^24 * n_rho / ((rho_max - rho_min) * u_z))
+ *   D    = round(-rho_min * 2^24 * n_rho / (rho_max - rho_min))
+ */
+int oracle_tables(const oracle_geometry *g, int n_theta, int n_rho, int32_t *C, int32_t *S,
+                  int64_t *D)
+{
+    if (!g || n_theta <= 0 || n_rho <= 0 || !(g->rho_max > g->rho_min))
+        return -1;
+    double two_k = ldexp(1.0, ORACLE_FRAC_BITS);
+    double span = g->rho_max - g->rho_min;
+    double cos_scale = two_k * (double)n_rho / (span * (double)g->phi_u_per_deg);
+    double sin_scale = two_k * (double)n_rho / (span * (double)g->z_u_per_mm);
+    for (int t = 0; t < n_theta; ++t) {
+        double theta = ((double)t + 0.5) * (M_PI / (double)n_theta);
+        C[t] = (int32_t)round_half_away(cos(theta) * cos_scale);
+        S[t] = (int32_t)round_half_away(sin(theta) * sin_scale);
+    }
+    *D = round_half_away(-g->rho_min * (two_k * (double)n_rho / span));
+    return 0;
+}
+
+/*
+ * Step A: strip address -> fixed-point (phi, z).  Radial vanes sit every
+ * 360/n_vanes degrees (Section 2), so phi is the vane angle; z is the centre
+ * of the strip.  Out-of-range addresses are encoded anyway (the find step
+ * rejects them).
+ */
+void oracle_encode(const oracle_geometry *g, const int32_t *vane, const int32_t *strip, int64_t n,
+                   int32_t *phi_q, int32_t *z_q)
+{
+    int64_t vane_step = (int64_t)360 * g->phi_u_per_deg / g->n_vanes;
+    for (int64_t i = 0; i < n; ++i) {
+        phi_q[i] = (int32_t)(vane_step * (int64_t)vane[i]);
+        z_q[i] = (int32_t)((int64_t)g->z_min_u + (int64_t)g->z_pitch_u * strip[i] +
+                           g->z_pitch_u / 2);
+    }
+}
+
+/* Whether an encoded hit lies inside the detector's coordinate box. */
+static int hit_is_valid(const oracle_geometry *g, int32_t phi, int32_t z)
+{
+    int64_t phi_end = (int64_t)360 * g->phi_u_per_deg;
+    int64_t z_end = (int64_t)g->z_min_u + (int64_t)g->n_z_strips * g->z_pitch_u;
+    return phi >= 0 && (int64_t)phi < phi_end && z >= g->z_min_u && (int64_t)z <= z_end;
+}
+
+/* The rho bin of one hit in one theta row. */
+static int64_t rho_bin(int32_t phi, int32_t z, int32_t c, int32_t s, int64_t d)
+{
+    int64_t value = (int64_t)phi * (int64_t)c + (int64_t)z * (int64_t)s + d;
+    return floor_div(value, (int64_t)1 << ORACLE_FRAC_BITS);
+}
+
+/*
+ * Step B alone: fill a zeroed int32 accumulator acc[n_theta][n_rho] from the
+ * valid hits; returns the number of dropped (out-of-range) votes.
+ */
+int64_t oracle_vote(const oracle_geometry *g, int n_theta, int n_rho, const int32_t *phi_q,
+                    const int32_t *z_q, int64_t n_hits, int32_t *acc)
+{
+    int32_t *C = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_theta);
+    int32_t *S = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_theta);
+    int64_t D = 0;
+    int64_t dropped = 0;
+    oracle_tables(g, n_theta, n_rho, C, S, &D);
+    memset(acc, 0, sizeof(int32_t) * (size_t)n_theta * (size_t)n_rho);
+    for (int64_t h = 0; h < n_hits; ++h) {
+        if (!hit_is_valid(g, phi_q[h], z_q[h]))
+            continue;
+        for (int t = 0; t < n_theta; ++t) {
+            int64_t b = rho_bin(phi_q[h], z_q[h], C[t], S[t], D);
+            if (b >= 0 && b < n_rho)
+                acc[(size_t)t * n_rho + (size_t)b] += 1;
+            else
+                dropped += 1;
+        }
+    }
+    free(C);
+    free(S);
+    return dropped;
+}
+
+/* FP64 continuous variant of step B: the bin from Eq. (1) in double precision,
+ * b = floor((phi_deg*cos(theta) + z_mm*sin(theta) - rho_min) / drho).  Used to
+ * check that the fixed-point bins agree within one bin.  bins[h*n_theta + t]. */
+void oracle_bins_fp64(const oracle_geometry *g, int n_theta, int n_rho, const int32_t *phi_q,
+                      const int32_t *z_q, int64_t n_hits, int64_t *bins)
+{
+    double drho = (g->rho_max - g->rho_min) / (double)n_rho;
+    for (int64_t h = 0; h < n_hits; ++h) {
+        double phi = (double)phi_q[h] / (double)g->phi_u_per_deg;
+        double z = (double)z_q[h] / (double)g->z_u_per_mm;
+        for (int t = 0; t < n_theta; ++t) {
+            double theta = ((double)t + 0.5) * (M_PI / (double)n_theta);
+            double rho = phi * cos(theta) + z * sin(theta);
+            bins[h * n_theta + t] = (int64_t)floor((rho - g->rho_min) / drho);
+        }
+    }
+}
+
+/* Fixed-point bins for every (hit, theta); same layout as oracle_bins_fp64. */
+void oracle_bins_fixed(const oracle_geometry *g, int n_theta, int n_rho, const int32_t *phi_q,
+                       const int32_t *z_q, int64_t n_hits, int64_t *bins)
+{
+    int32_t *C = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_theta);
+    int32_t *S = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_theta);
+    int64_t D = 0;
+    oracle_tables(g, n_theta, n_rho, C, S, &D);
+    for (int64_t h = 0; h < n_hits; ++h)
+        for (int t = 0; t < n_theta; ++t)
+            bins[h * n_theta + t] = rho_bin(phi_q[h], z_q[h], C[t], S[t], D);
+    free(C);
+    free(S);
+}
+
+/* ----------------------------------------------------------------- step C */
+
+static int32_t acc_at(const int32_t *acc, int n_theta, int n_rho, int t, int b)
+{
+    if (t < 0 || t >= n_theta || b < 0 || b >= n_rho)
+        return 0; /* no neighbour across an edge; counts are >= 0 and peaks >= T >= 1 */
+    return acc[(size_t)t * n_rho + (size_t)b];
+}
+
+typedef struct {
+    int32_t votes;
+    int32_t t;
+    int32_t b;
+} cand_t;
+
+/* votes descending, then theta ascending, then rho ascending */
+static int cand_cmp(const void *pa, const void *pb)
+{
+    const cand_t *a = (const cand_t *)pa;
+    const cand_t *b = (const cand_t *)pb;
+    if (a->votes != b->votes)
+        return a->votes > b->votes ? -1 : 1;
+    if (a->t != b->t)
+        return a->t < b->t ? -1 : 1;
+    if (a->b != b->b)
+        return a->b < b->b ? -1 : 1;
+    return 0;
+}
+
+/*
+ * Step C on a given accumulator.  A bin (t, b) with v = acc[t][b] >= T is a
+ * peak iff v is strictly greater than each of its neighbours that come earlier
+ * in row-major order, (t-1, b-1), (t-1, b), (t-1, b+1), (t, b-1), and greater
+ * than or equal to each later one, (t, b+1), (t+1, b-1), (t+1, b), (t+1, b+1).
+ * Peaks are sorted (votes desc, t asc, b asc); the first max_peaks are kept.
+ * Returns the number of peaks found (before truncation); *n_kept gets the kept
+ * count.
+ */
+int32_t oracle_peaks(const int32_t *acc, int n_theta, int n_rho, int32_t threshold,
+                     int32_t max_peaks, oracle_peak *peaks, int32_t *n_kept)
+{
+    size_t cap = 64, n = 0;
+    cand_t *cand = (cand_t *)malloc(sizeof(cand_t) * cap);
+    for (int t = 0; t < n_theta; ++t) {
+        for (int b = 0; b < n_rho; ++b) {
+            int32_t v = acc[(size_t)t * n_rho + (size_t)b];
+            if (v < threshold)
+                continue;
+            int ok = v > acc_at(acc, n_theta, n_rho, t - 1, b - 1) &&
+                     v > acc_at(acc, n_theta, n_rho, t - 1, b) &&
+                     v > acc_at(acc, n_theta, n_rho, t - 1, b + 1) &&
+                     v > acc_at(acc, n_theta, n_rho, t, b - 1) &&
+                     v >= acc_at(acc, n_theta, n_rho, t, b + 1) &&
+                     v >= acc_at(acc, n_theta, n_rho, t + 1, b - 1) &&
+                     v >= acc_at(acc, n_theta, n_rho, t + 1, b) &&
+                     v >= acc_at(acc, n_theta, n_rho, t + 1, b + 1);
+            if (!ok)
+                continue;
+            if (n == cap) {
+                cap *= 2;
+                cand = (cand_t *)realloc(cand, sizeof(cand_t) * cap);
+            }
+            cand[n].votes = v;
+            cand[n].t = t;
+            cand[n].b = b;
+            ++n;
+        }
+    }
+    qsort(cand, n, sizeof(cand_t), cand_cmp);
+    int32_t kept = (int32_t)(n < (size_t)max_peaks ? n : (size_t)max_peaks);
+    for (int32_t i = 0; i < kept; ++i) {
+        peaks[i].theta = (uint16_t)cand[i].t;
+        peaks[i].rho = (uint16_t)cand[i].b;
+        peaks[i].votes = cand[i].votes;
+        peaks[i].n_hits = 0;
+        peaks[i].hit_begin = 0;
+    }
+    free(cand);
+    *n_kept = kept;
+    return (int32_t)n;
+}
+
+/* --------------------------------------------------------------- step A-D */
+
+/*
+ * One time window through steps B-D.
+ *   acc        : optional int32[n_theta*n_rho] (NULL: use a private buffer)
+ *   peaks      : out, max_peaks entries
+ *   hit_track  : out, per hit: peak index (0..n_kept-1), -1 unassigned,
+ *                -2 rejected (outside the coordinate box)
+ *   track_hits : out, a permutation of 0..n_hits-1: the hits of peak 0 in
+ *                increasing index, then of peak 1, ..., then the unassigned
+ *                hits, then the rejected ones.  peaks[p].hit_begin/n_hits
+ *                index into it.
+ * Returns 0, or -1 on bad arguments.
+ */
+int oracle_find_window(const oracle_geometry *g, int n_theta, int n_rho,
+                       const oracle_thresholds *th, const int32_t *phi_q, const int32_t *z_q,
+                       int64_t n_hits, int32_t *acc_out, int64_t *n_dropped, oracle_peak *peaks,
+                       int32_t *n_peaks, int32_t *n_found, int32_t *hit_track,
+                       int32_t *track_hits, uint32_t *status)
+{
+    if (!g || !th || n_theta <= 0 || n_rho <= 0 || th->vote_threshold < 1 ||
+        th->assoc_tol_bins < 0 || th->max_peaks < 0)
+        return -1;
+    uint32_t st = 0;
+    int32_t *acc = acc_out;
+    if (!acc)
+        acc = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_theta * (size_t)n_rho);
+
+    /* B: vote */
+    int64_t dropped = oracle_vote(g, n_theta, n_rho, phi_q, z_q, n_hits, acc);
+    for (int64_t h = 0; h < n_hits; ++h)
+        if (!hit_is_valid(g, phi_q[h], z_q[h]))
+            st |= ORACLE_WIN_HIT_OUT_OF_RANGE;
+    if (dropped > 0)
+        st |= ORACLE_WIN_VOTE_OUT_OF_RANGE;
+
+    /* C: peaks */
+    int32_t kept = 0;
+    int32_t found = oracle_peaks(acc, n_theta, n_rho, th->vote_threshold, th->max_peaks, peaks,
+                                 &kept);
+    if (found > th->max_peaks)
+        st |= ORACLE_WIN_PEAK_OVERFLOW;
+
+    /* D: association, first matching peak in the sorted order */
+    int32_t *C = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_theta);
+    int32_t *S = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_theta);
+    int64_t D = 0;
+    oracle_tables(g, n_theta, n_rho, C, S, &D);
+    for (int64_t h = 0; h < n_hits; ++h) {
+        if (!hit_is_valid(g, phi_q[h], z_q[h])) {
+            hit_track[h] = -2;
+            continue;
+        }
+        hit_track[h] = -1;
+        for (int32_t p = 0; p < kept; ++p) {
+            int t = peaks[p].theta;
+            int64_t bh = rho_bin(phi_q[h], z_q[h], C[t], S[t], D);
+            int64_t diff = bh - (int64_t)peaks[p].rho;
+            if (diff < 0)
+                diff = -diff;
+            if (diff <= th->assoc_tol_bins) {
+                hit_track[h] = p;
+                break;
+            }
+        }
+    }
+    /* per-peak compaction, each group in increasing hit index */
+    int32_t pos = 0;
+    for (int32_t p = 0; p < kept; ++p) {
+        peaks[p].hit_begin = pos;
+        for (int64_t h = 0; h < n_hits; ++h)
+            if (hit_track[h] == p)
+                track_hits[pos++] = (int32_t)h;
+        peaks[p].n_hits = pos - peaks[p].hit_begin;
+    }
+    for (int64_t h = 0; h < n_hits; ++h)
+        if (hit_track[h] == -1)
+            track_hits[pos++] = (int32_t)h;
+    for (int64_t h = 0; h < n_hits; ++h)
+        if (hit_track[h] == -2)
+            track_hits[pos++] = (int32_t)h;
+
+    free(C);
+    free(S);
+    if (!acc_out)
+        free(acc);
+    if (n_dropped)
+        *n_dropped = dropped;
+    *n_peaks = kept;
+    if (n_found)
+        *n_found = found;
+    *status = st;
+    return 0;
+}
+
+/*
+ * A batch of windows in CSR form (window w owns hits offsets[w]..offsets[w+1]),
+ * each processed independently by oracle_find_window.  Outputs use the same
+ * layout as the library's: peaks[w*max_peaks + i], n_peaks[w], n_found[w],
+ * hit_track[h] and track_hits[h] window-local, status[w]; acc (optional) is
+ * [n_windows][n_theta][n_rho].  Returns 0, or -1 on bad arguments.
+ */
+int oracle_find_batch(const oracle_geometry *g, int n_theta, int n_rho,
+                      const oracle_thresholds *th, const int32_t *phi_q, const int32_t *z_q,
+                      const int64_t *offsets, int64_t n_windows, int32_t *acc, oracle_peak *peaks,
+                      int32_t *n_peaks, int32_t *n_found, int32_t *hit_track,
+                      int32_t *track_hits, uint32_t *status)
+{
+    for (int64_t w = 0; w < n_windows; ++w) {
+        int64_t b = offsets[w], e = offsets[w + 1];
+        if (b < 0 || e < b)
+            return -1;
+        int rc = oracle_find_window(
+            g, n_theta, n_rho, th, phi_q + b, z_q + b, e - b,
+            acc ? acc + (size_t)w * n_theta * n_rho : NULL, NULL,
+            peaks + (size_t)w * th->max_peaks, n_peaks + w, n_found ? n_found + w : NULL,
+            hit_track + b, track_hits + b, status + w);
+        if (rc != 0)
+            return rc;
+    }
+    return 0;
+}
