@@ -95,6 +95,19 @@ def test_fixed_point_bins_within_one_bin_of_fp64(n_theta, n_rho):
     np.testing.assert_array_equal(fp[safe], ref[safe])
 
 
+@pytest.mark.parametrize("n_theta,n_rho", SHAPES)
+def test_tables_round_to_nearest(n_theta, n_rho):
+    """The fixed-point cos/sin factors of Eq. (1) are rounded to the nearest
+    integer: each entry is within half a unit of the real factor
+    cos(theta_t) * 2^24 * n_rho / (1000 deg * 200 u/deg), and likewise for sin."""
+    C, S, D = oracle.tables(G, n_theta, n_rho)
+    theta = (np.arange(n_theta) + 0.5) * math.pi / n_theta
+    scale = 2.0 ** 24 * n_rho / (1000.0 * 200.0)
+    assert np.abs(C - np.cos(theta) * scale).max() <= 0.5 + 1e-6
+    assert np.abs(S - np.sin(theta) * scale).max() <= 0.5 + 1e-6
+    assert D == (n_rho // 2) << 24          # rho_min = -500 is exactly n_rho/2 bins below 0
+
+
 def test_fixed_point_edges_of_rho_range():
     """Section 5: rho in [-500, 500) over n_rho bins; rho_min maps to bin 0 and
     a point just below rho_max to bin n_rho - 1.  With phi = 0, z = 0, rho = 0
@@ -320,8 +333,19 @@ def test_association_two_lines_first_peak_wins():
     pb, zb = _line_hits(thb, rhob, range(1, 40, 3))      # 13 hits
     keep_a = np.abs(za) < 38900
     keep_b = np.abs(zb) < 38900
-    phi = np.concatenate([pa[keep_a], pb[keep_b], np.array([9000], np.int32)])
-    z = np.concatenate([za[keep_a], zb[keep_b], np.array([30000], np.int32)])
+    # off-line probes near line A at theta_a: +1 bin (inside the tolerance of one
+    # bin) and +2 bins (outside), both at a bin centre, on vanes 5 and 33
+    probes_phi, probes_z = [], []
+    for k, dbins in ((5, 1), (33, 2), (7, -1), (31, -2)):
+        ph = 9.0 * k
+        rr = rhoa + dbins * drho
+        zz = (rr - ph * math.cos(math.radians(tha))) / math.sin(math.radians(tha))
+        probes_phi.append(1800 * k)
+        probes_z.append(int(round(zz * 200.0)))
+    phi = np.concatenate([pa[keep_a], pb[keep_b], np.array(probes_phi, np.int32),
+                          np.array([9000], np.int32)])
+    z = np.concatenate([za[keep_a], zb[keep_b], np.array(probes_z, np.int32),
+                        np.array([30000], np.int32)])
     r = oracle.find_window(G, n_theta, n_rho, phi, z)
     p0, p1 = r["peaks"][0], r["peaks"][1]
     assert (int(p0["theta"]), int(p0["rho"]), int(p0["votes"])) == (ta, ba, int(keep_a.sum()))
@@ -341,6 +365,10 @@ def test_association_two_lines_first_peak_wins():
         else:
             assert r["hit_track"][h] not in (0, 1)
     assert checked >= len(phi) - 3
+    n_ab = int(keep_a.sum() + keep_b.sum())
+    ht = r["hit_track"]
+    assert ht[n_ab] == 0 and ht[n_ab + 2] == 0          # one bin off: on the line
+    assert ht[n_ab + 1] != 0 and ht[n_ab + 3] != 0      # two bins off: not on it
     assert r["hit_track"][len(phi) - 1] == -1 or r["hit_track"][len(phi) - 1] >= 2
 
 
