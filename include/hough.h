@@ -1,0 +1,259 @@
+/*
+ * hough.h -- C ABI of the GB300 track-finding library (libhough).
+ *
+ * The library runs the data-parallel hot path of the J-PARC muon g-2/EDM
+ * positron track-finder (arXiv 2511.02742) on one GPU: per time window,
+ *   A. encode strip-level hits to fixed-point (phi, z)        (Section 2, Section 5)
+ *   B. Hough voting rho = phi cos(theta) + z sin(theta)      (Section 4, Eq. (1))
+ *      into an n_theta x n_rho accumulator over theta in [0, 180) degrees
+ *      and rho in [rho_min, rho_max)                          (Section 5 binning)
+ *   C. peak extraction                                       (Section 4, Section 5)
+ *   D. association of the hits that lie on each peak's line  (Section 5 seeds)
+ * All arithmetic is integer, so results are bit-exact and deterministic.
+ *
+ * Conventions
+ *   - Every call returns HOUGH_OK (0) or a negative hough_status; nothing
+ *     aborts.  Arguments the host can check are checked before any launch.
+ *   - Pointers documented "device" must point to memory of the context's
+ *     device; "host" pointers to host memory (pinned memory lets copies
+ *     overlap with compute).  The caller owns every buffer it passes in; the
+ *     library owns only what it allocates itself and frees it in
+ *     hough_destroy / hough_plan_destroy.
+ *   - Device work is asynchronous on the given stream (a cudaStream_t passed
+ *     as void*; NULL = legacy default stream).  Per-window conditions found on
+ *     the device are reported in tracks_out->window_status, not as return codes.
+ *   - A context may be used from one host thread at a time.
+ */
+#ifndef HOUGH_H
+#define HOUGH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Fraction bits of the fixed-point cos/sin tables (see hough_tables). */
+#define HOUGH_FRAC_BITS 24
+
+/* Largest accumulator sides and peak list the kernels accept. */
+#define HOUGH_MAX_THETA 4096
+#define HOUGH_MAX_RHO 2048
+#define HOUGH_MAX_PEAKS 256
+
+typedef enum hough_status {
+    HOUGH_OK = 0,
+    HOUGH_ERR_INVALID_ARG = -1,       /* NULL pointer, negative size, bad field   */
+    HOUGH_ERR_ALLOC = -2,             /* device or host allocation failed         */
+    HOUGH_ERR_CUDA = -3,              /* a CUDA runtime call failed               */
+    HOUGH_ERR_TIMEOUT = -4,           /* a bounded device wait gave up            */
+    HOUGH_ERR_UNSUPPORTED_SHAPE = -5, /* n_theta / n_rho / max_peaks out of range */
+    HOUGH_ERR_NO_DEVICE = -6          /* no usable CUDA device                    */
+} hough_status;
+
+/* Per-window flags, OR-ed into tracks_out->window_status[w]. */
+#define HOUGH_WIN_PEAK_OVERFLOW 1u     /* more peaks found than max_peaks; best kept     */
+#define HOUGH_WIN_HIT_OUT_OF_RANGE 2u  /* a hit lies outside the detector box; ignored   */
+#define HOUGH_WIN_VOTE_OUT_OF_RANGE 4u /* a valid hit's vote fell outside [0, n_rho)    */
+#define HOUGH_WIN_BAD_OFFSETS 8u       /* offsets not ordered or beyond n_hits; skipped  */
+
+/* hough_thresholds.flags */
+#define HOUGH_FLAG_EXPORT_ACC 1u /* write the full int32 accumulator (tracks_out->acc) */
+
+/*
+ * Detector geometry and fixed-point units (Section 2).  Defaults for the
+ * J-PARC detector: n_vanes = 40 radial vanes, n_z_strips = 2048 z strips per
+ * vane at z_pitch_u = 38 units (0.19 mm) starting at z_min_u = -38912
+ * (-194.56 mm), phi_u_per_deg = z_u_per_mm = 200 (1 unit = 1/200 degree or
+ * 1/200 mm), rho range [-500, 500) (Section 5).
+ * A hit is inside the detector box when 0 <= phi < 360 deg and
+ * z_min <= z <= z_min + n_z_strips * z_pitch (in units).
+ */
+typedef struct hough_geometry {
+    int32_t n_vanes;
+    int32_t n_z_strips;
+    int32_t z_pitch_u;
+    int32_t z_min_u;
+    int32_t phi_u_per_deg;
+    int32_t z_u_per_mm;
+    double rho_min;
+    double rho_max;
+} hough_geometry;
+
+/*
+ * Peak and association parameters (Section 4, Section 5).
+ *   vote_threshold >= 1: a peak needs at least this many votes;
+ *   assoc_tol_bins >= 0: a hit lies on a peak's line when its rho bin in the
+ *                        peak's theta row is within this many bins;
+ *   max_peaks in [0, HOUGH_MAX_PEAKS]: peaks kept per window;
+ *   flags: HOUGH_FLAG_*.
+ */
+typedef struct hough_thresholds {
+    int32_t vote_threshold;
+    int32_t assoc_tol_bins;
+    int32_t max_peaks;
+    uint32_t flags;
+} hough_thresholds;
+
+/* One peak: theta row, rho bin, its vote count, and the slice of track_hits
+ * (window-local, starting at hit_begin, n_hits long) holding its hits. */
+typedef struct hough_peak {
+    uint16_t theta;
+    uint16_t rho;
+    int32_t votes;
+    int32_t n_hits;
+    int32_t hit_begin;
+} hough_peak;
+
+/*
+ * Hits in structure-of-arrays form, device pointers, n_hits long.  Give
+ * either the encoded pair (phi_q, z_q) or the strip addresses (vane, strip);
+ * when vane and strip are both non-NULL they are used and encoded on the fly
+ * (phi = vane * 360/n_vanes deg, z = centre of the strip), else phi_q and z_q.
+ */
+typedef struct hough_hits {
+    const int32_t *phi_q;
+    const int32_t *z_q;
+    const int32_t *vane;
+    const int32_t *strip;
+    int64_t n_hits;
+} hough_hits;
+
+/*
+ * Outputs, caller-owned device buffers.  For n_windows windows and n_hits hits:
+ *   peaks[n_windows * max_peaks]  window w's peaks at [w*max_peaks, ...+n_peaks[w]),
+ *                                 sorted by votes desc, theta asc, rho asc;
+ *   n_peaks[n_windows]            peaks kept;
+ *   n_found[n_windows]            peaks found before truncation (may be NULL);
+ *   hit_track[n_hits]             per hit: window-local peak index, -1 if on
+ *                                 no peak's line, -2 if outside the detector box;
+ *   track_hits[n_hits]            per window, a permutation of the window-local
+ *                                 hit indices: the hits of peak 0 in increasing
+ *                                 order, then peak 1, ..., then the -1 hits, then
+ *                                 the -2 hits;
+ *   window_status[n_windows]      HOUGH_WIN_* flags;
+ *   acc                           with HOUGH_FLAG_EXPORT_ACC, int32
+ *                                 [n_windows][n_theta][n_rho]; else ignored.
+ * Entries past n_peaks[w] are not written.
+ */
+typedef struct hough_tracks {
+    hough_peak *peaks;
+    int32_t *n_peaks;
+    int32_t *n_found;
+    int32_t *hit_track;
+    int32_t *track_hits;
+    uint32_t *window_status;
+    int32_t *acc;
+} hough_tracks;
+
+/* Launch shape of the find kernel; 0 in a field means "library default". */
+typedef struct hough_launch {
+    int32_t threads;      /* threads per CTA: 256, 512 or 1024                     */
+    int32_t word_rows;    /* word rows of the shared accumulator tile: 32, 64 or 128   */
+    int32_t hit_stage;    /* hits held in shared memory per stage (multiple of 256)  */
+    int32_t ctas_per_sm;  /* resident CTAs per SM (1..4); capped by occupancy       */
+} hough_launch;
+
+typedef struct hough_ctx hough_ctx;
+typedef struct hough_plan hough_plan;
+
+/*
+ * Fixed-point tables of Eq. (1) with the Section 5 binning, host only (no GPU).
+ * theta_t = (t + 1/2) * 180/n_theta degrees; with span = rho_max - rho_min,
+ *   C[t] = round(cos(theta_t) * 2^24 * n_rho / (span * phi_u_per_deg))
+ *   S[t] = round(sin(theta_t) * 2^24 * n_rho / (span * z_u_per_mm))
+ *   D    = round(-rho_min * 2^24 * n_rho / span)
+ * rounding half away from zero.  A valid hit (phi, z) votes in row t for bin
+ *   b = floor((phi*C[t] + z*S[t] + D) / 2^24)   (64-bit arithmetic),
+ * if 0 <= b < n_rho.  C and S are host arrays of n_theta entries.
+ */
+int hough_tables(const hough_geometry *g, int n_theta, int n_rho, int32_t *C, int32_t *S,
+                 int64_t *D);
+
+/*
+ * Create a context on the current CUDA device for one accumulator shape
+ * (Section 5: 180 x 1000 in the paper; any 1 <= n_theta <= HOUGH_MAX_THETA,
+ * 4 <= n_rho <= HOUGH_MAX_RHO with n_rho % 4 == 0).  Copies g and th, builds
+ * the tables on the device.  *out receives the context; release it with
+ * hough_destroy.  Errors: INVALID_ARG, UNSUPPORTED_SHAPE, NO_DEVICE, ALLOC, CUDA.
+ */
+int hough_create(const hough_geometry *g, int n_theta, int n_rho, const hough_thresholds *th,
+                 hough_ctx **out);
+
+/* Release a context and everything it allocated.  NULL is a no-op.  The caller
+ * must make sure no work using the context is still running. */
+void hough_destroy(hough_ctx *ctx);
+
+/*
+ * Step A alone (Section 2 geometry, Section 5 phi = atan(y/x)): device arrays
+ * vane[n], strip[n] -> phi_q[n], z_q[n] (device).  Addresses outside the
+ * detector give values the find step rejects.  Asynchronous on stream.
+ */
+int hough_encode(hough_ctx *ctx, const int32_t *vane, const int32_t *strip, int64_t n,
+                 int32_t *phi_q, int32_t *z_q, void *stream);
+
+/*
+ * Steps B-D for n_windows windows (Section 4, Section 5; one window per
+ * independent unit of work as in Section 6).  window_offsets is a device
+ * array of n_windows + 1 int64: window w owns hits [offsets[w], offsets[w+1]).
+ * Offsets must be non-decreasing within [0, hits->n_hits]; a window whose own
+ * pair is decreasing or out of range gets HOUGH_WIN_BAD_OFFSETS and no output
+ * (no memory outside [0, n_hits) is touched).  Windows must not overlap: two
+ * windows sharing a hit write the same hit_track/track_hits slots.
+ * Asynchronous on stream; results are identical for every launch shape,
+ * stream and batch.
+ * Errors: INVALID_ARG (bad pointers/sizes), CUDA (launch failed).
+ */
+int hough_find(hough_ctx *ctx, const hough_hits *hits, const int64_t *window_offsets,
+               int64_t n_windows, const hough_tracks *tracks_out, void *stream);
+
+/*
+ * hough_find on HOST buffers: the same arguments, but every pointer in hits,
+ * window_offsets and tracks_out is a host pointer.  The library copies inputs
+ * to device staging buffers it owns, runs the path, copies the results back
+ * and synchronises before returning (the end-to-end form).  Work is split
+ * into chunks of windows so that copies overlap compute.
+ */
+int hough_find_host(hough_ctx *ctx, const hough_hits *hits, const int64_t *window_offsets,
+                    int64_t n_windows, const hough_tracks *tracks_out, void *stream);
+
+/*
+ * A plan is hough_find (optionally preceded by nothing else) captured once
+ * into a CUDA graph bound to these exact device buffers: one persistent
+ * kernel over all windows.  hough_plan_launch replays it on any stream.
+ * The buffers must stay valid while the plan exists.  Errors as hough_find.
+ */
+int hough_plan_create(hough_ctx *ctx, const hough_hits *hits, const int64_t *window_offsets,
+                      int64_t n_windows, const hough_tracks *tracks_out, void *stream,
+                      hough_plan **out);
+int hough_plan_launch(hough_plan *plan, void *stream);
+void hough_plan_destroy(hough_plan *plan);
+
+/* Read or set the launch shape used by later calls (0 fields = defaults). */
+int hough_get_launch(const hough_ctx *ctx, hough_launch *out);
+int hough_set_launch(hough_ctx *ctx, const hough_launch *cfg);
+
+/*
+ * Time every supported launch shape on this batch (iters runs each, CUDA
+ * events on stream), keep the fastest in the context and return it in *best
+ * (may be NULL).  Outputs are overwritten with the (identical) results.
+ */
+int hough_autotune(hough_ctx *ctx, const hough_hits *hits, const int64_t *window_offsets,
+                   int64_t n_windows, const hough_tracks *tracks_out, void *stream, int iters,
+                   hough_launch *best);
+
+/* Human-readable name of a hough_status value. */
+const char *hough_status_string(int status);
+
+/* The status of the last failing call on ctx (HOUGH_OK if none). */
+int hough_last_error(const hough_ctx *ctx);
+
+/* Number of kernel launches the library issued on ctx (for accounting). */
+int64_t hough_launch_count(const hough_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HOUGH_H */

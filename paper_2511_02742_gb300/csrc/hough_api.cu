@@ -1,0 +1,668 @@
+// hough_api.cu -- host side of the C ABI declared in include/hough.h.
+//
+// The context owns: the fixed-point tables on the device, one scheduling
+// counter pair per stream it has launched on (the persistent kernel resets
+// its own pair when it ends, so no memset is needed between launches), the
+// device staging buffers of hough_find_host, and the chosen launch shape.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <unordered_map>
+#include <vector>
+
+#include "hough.h"
+#include "hough_kernels.cuh"
+
+struct hough_ctx {
+    int device = 0;
+    hough_geometry g{};
+    hough_thresholds th{};
+    int n_theta = 0, n_rho = 0;
+    std::vector<int32_t> C, S;
+    long long D = 0;
+    int32_t *d_C = nullptr, *d_S = nullptr;
+    hough_launch launch{};
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    std::unordered_map<cudaStream_t, unsigned int *> counters;
+    int last_error = HOUGH_OK;
+    long long launches = 0;
+    // hough_find_host staging (device), grown on demand
+    void *stage_dev = nullptr;
+    size_t stage_bytes = 0;
+    cudaStream_t host_streams[2] = {nullptr, nullptr};
+    cudaEvent_t host_events[2] = {nullptr, nullptr};
+};
+
+struct hough_plan {
+    hough_ctx *ctx = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned int *counter = nullptr;
+};
+
+namespace {
+
+int fail(hough_ctx *ctx, int code)
+{
+    if (ctx && code != HOUGH_OK)
+        ctx->last_error = code;
+    return code;
+}
+
+long long round_half_away(double x)
+{
+    return x >= 0.0 ? (long long)std::floor(x + 0.5) : -(long long)std::floor(-x + 0.5);
+}
+
+bool geometry_ok(const hough_geometry *g)
+{
+    return g && g->n_vanes > 0 && g->n_z_strips > 0 && g->z_pitch_u > 0 && g->phi_u_per_deg > 0 &&
+           g->z_u_per_mm > 0 && std::isfinite(g->rho_min) && std::isfinite(g->rho_max) &&
+           g->rho_max > g->rho_min && (360LL * g->phi_u_per_deg) % g->n_vanes == 0;
+}
+
+int next_pow2(int x)
+{
+    int n = 1;
+    while (n < x)
+        n <<= 1;
+    return n;
+}
+
+int stride_for(int n_rho)
+{
+    // smallest stride >= n_rho with stride = 1 (mod 32)
+    int s = n_rho;
+    while ((s & 31) != 1)
+        ++s;
+    return s;
+}
+
+// Fill in defaults and check a launch shape against the device limits.
+int resolve_launch(const hough_ctx *ctx, const hough_launch &in, hough_launch &out, size_t &smem)
+{
+    hough_launch l = in;
+    if (l.threads == 0)
+        l.threads = 512;
+    if (l.hit_stage == 0)
+        l.hit_stage = 2048;
+    if (l.ctas_per_sm == 0)
+        l.ctas_per_sm = 1;
+    if (l.word_rows == 0) {
+        // the largest tile that fits, as long as 16-bit tiles do not pass n_theta
+        l.word_rows = 32;
+        for (int wr : {128, 64}) {
+            hk::SmemLayout L = hk::smem_layout(wr, stride_for(ctx->n_rho), l.hit_stage, ctx->n_rho);
+            if (L.total <= ctx->smem_optin / (size_t)l.ctas_per_sm && ctx->n_theta >= 2 * wr) {
+                l.word_rows = wr;
+                break;
+            }
+        }
+    }
+    if (!(l.threads == 256 || l.threads == 512 || l.threads == 1024))
+        return HOUGH_ERR_INVALID_ARG;
+    if (!(l.word_rows == 32 || l.word_rows == 64 || l.word_rows == 128))
+        return HOUGH_ERR_INVALID_ARG;
+    if (l.hit_stage < 256 || l.hit_stage % 256 != 0 || l.hit_stage > 16384)
+        return HOUGH_ERR_INVALID_ARG;
+    if (l.ctas_per_sm < 1 || l.ctas_per_sm > 4)
+        return HOUGH_ERR_INVALID_ARG;
+    hk::SmemLayout L = hk::smem_layout(l.word_rows, stride_for(ctx->n_rho), l.hit_stage, ctx->n_rho);
+    if (L.total > ctx->smem_optin)
+        return HOUGH_ERR_UNSUPPORTED_SHAPE;
+    out = l;
+    smem = L.total;
+    return HOUGH_OK;
+}
+
+bool tracks_ok(const hough_ctx *ctx, const hough_tracks *t)
+{
+    if (!t || !t->n_peaks || !t->hit_track || !t->track_hits || !t->window_status)
+        return false;
+    if (ctx->th.max_peaks > 0 && !t->peaks)
+        return false;
+    if ((ctx->th.flags & HOUGH_FLAG_EXPORT_ACC) && !t->acc)
+        return false;
+    return true;
+}
+
+bool hits_ok(const hough_hits *h)
+{
+    if (!h || h->n_hits < 0)
+        return false;
+    bool raw = h->vane && h->strip;
+    if (!raw && h->n_hits > 0 && !(h->phi_q && h->z_q))
+        return false;
+    return true;
+}
+
+hk::KParams make_params(const hough_ctx *ctx, const hough_hits *hits, const int64_t *offsets,
+                        int64_t n_windows, const hough_tracks *out, unsigned int *counter,
+                        const hough_launch &l)
+{
+    hk::KParams p{};
+    const hough_geometry &g = ctx->g;
+    bool raw = hits->vane && hits->strip;
+    p.a = raw ? hits->vane : hits->phi_q;
+    p.b = raw ? hits->strip : hits->z_q;
+    p.n_hits = hits->n_hits;
+    p.raw = raw ? 1 : 0;
+    p.vane_step = (int)(360LL * g.phi_u_per_deg / g.n_vanes);
+    p.z_min_u = g.z_min_u;
+    p.z_pitch_u = g.z_pitch_u;
+    p.z_half = g.z_pitch_u / 2;
+    p.phi_end = 360LL * g.phi_u_per_deg;
+    p.z_end = (long long)g.z_min_u + (long long)g.n_z_strips * g.z_pitch_u;
+    p.offsets = reinterpret_cast<const long long *>(offsets);
+    p.n_windows = n_windows;
+    p.C = ctx->d_C;
+    p.S = ctx->d_S;
+    p.D = ctx->D;
+    p.n_theta = ctx->n_theta;
+    p.n_rho = ctx->n_rho;
+    p.T = ctx->th.vote_threshold;
+    p.tol = ctx->th.assoc_tol_bins;
+    p.max_peaks = ctx->th.max_peaks;
+    p.export_acc = (ctx->th.flags & HOUGH_FLAG_EXPORT_ACC) ? 1 : 0;
+    p.peaks = out->peaks;
+    p.n_peaks = out->n_peaks;
+    p.n_found = out->n_found;
+    p.hit_track = out->hit_track;
+    p.track_hits = out->track_hits;
+    p.status = out->window_status;
+    p.acc = out->acc;
+    p.work = counter;
+    p.word_rows = l.word_rows;
+    p.stride = stride_for(ctx->n_rho);
+    p.hit_stage = l.hit_stage;
+    p.kp = std::max(32, next_pow2(std::max(1, ctx->th.max_peaks)));
+    return p;
+}
+
+struct Prepared {
+    hough_launch l;
+    size_t smem;
+    unsigned grid;
+};
+
+// Resolve a launch shape, raise the kernel's shared-memory limit and size the
+// persistent grid (not stream operations, so this runs outside any capture).
+int prepare_find(hough_ctx *ctx, int64_t n_windows, const hough_launch &req, Prepared &pr)
+{
+    int rc = resolve_launch(ctx, req, pr.l, pr.smem);
+    if (rc != HOUGH_OK)
+        return rc;
+    if (cudaFuncSetAttribute(hk::find_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)pr.smem) != cudaSuccess)
+        return HOUGH_ERR_CUDA;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hk::find_kernel, pr.l.threads,
+                                                      pr.smem) != cudaSuccess ||
+        occ < 1)
+        return HOUGH_ERR_UNSUPPORTED_SHAPE;
+    long long grid = (long long)ctx->num_sms * std::min(occ, pr.l.ctas_per_sm);
+    pr.grid = (unsigned)std::max<long long>(1, std::min<long long>(grid, n_windows));
+    return HOUGH_OK;
+}
+
+int enqueue_find(hough_ctx *ctx, const hough_hits *hits, const int64_t *offsets,
+                 int64_t n_windows, const hough_tracks *out, cudaStream_t s,
+                 unsigned int *counter, const Prepared &pr)
+{
+    hk::KParams p = make_params(ctx, hits, offsets, n_windows, out, counter, pr.l);
+    hk::find_kernel<<<pr.grid, pr.l.threads, pr.smem, s>>>(p);
+    if (cudaGetLastError() != cudaSuccess)
+        return HOUGH_ERR_CUDA;
+    ctx->launches += 1;
+    return HOUGH_OK;
+}
+
+int launch_find(hough_ctx *ctx, const hough_hits *hits, const int64_t *offsets, int64_t n_windows,
+                const hough_tracks *out, cudaStream_t s, unsigned int *counter,
+                const hough_launch &req)
+{
+    Prepared pr{};
+    int rc = prepare_find(ctx, n_windows, req, pr);
+    if (rc != HOUGH_OK)
+        return rc;
+    return enqueue_find(ctx, hits, offsets, n_windows, out, s, counter, pr);
+}
+
+unsigned int *counter_for(hough_ctx *ctx, cudaStream_t s)
+{
+    auto it = ctx->counters.find(s);
+    if (it != ctx->counters.end())
+        return it->second;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (s && cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+        return nullptr;   // cannot allocate inside a capture; use a plan
+    unsigned int *c = nullptr;
+    if (cudaMalloc(&c, 2 * sizeof(unsigned int)) != cudaSuccess)
+        return nullptr;
+    if (cudaMemset(c, 0, 2 * sizeof(unsigned int)) != cudaSuccess) {
+        cudaFree(c);
+        return nullptr;
+    }
+    ctx->counters[s] = c;
+    return c;
+}
+
+int check_find_args(hough_ctx *ctx, const hough_hits *hits, const int64_t *offsets,
+                    int64_t n_windows, const hough_tracks *out)
+{
+    if (!ctx || !hits_ok(hits) || n_windows < 0 || n_windows >= (1ll << 31) - 65536 ||
+        (n_windows > 0 && !offsets) || !tracks_ok(ctx, out))
+        return HOUGH_ERR_INVALID_ARG;
+    return HOUGH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hough_tables(const hough_geometry *g, int n_theta, int n_rho, int32_t *C, int32_t *S,
+                 int64_t *D)
+{
+    if (!geometry_ok(g) || n_theta <= 0 || n_rho <= 0 || !C || !S || !D)
+        return HOUGH_ERR_INVALID_ARG;
+    const double two_k = std::ldexp(1.0, HOUGH_FRAC_BITS);
+    const double span = g->rho_max - g->rho_min;
+    const double cs = two_k * (double)n_rho / (span * (double)g->phi_u_per_deg);
+    const double ss = two_k * (double)n_rho / (span * (double)g->z_u_per_mm);
+    const double step = M_PI / (double)n_theta;
+    for (int t = 0; t < n_theta; ++t) {
+        double th = ((double)t + 0.5) * step;
+        double c = std::cos(th) * cs, s = std::sin(th) * ss;
+        if (!(std::fabs(c) < 2147483647.0 && std::fabs(s) < 2147483647.0))
+            return HOUGH_ERR_UNSUPPORTED_SHAPE;
+        C[t] = (int32_t)round_half_away(c);
+        S[t] = (int32_t)round_half_away(s);
+    }
+    *D = (int64_t)round_half_away(-g->rho_min * (two_k * (double)n_rho / span));
+    return HOUGH_OK;
+}
+
+int hough_create(const hough_geometry *g, int n_theta, int n_rho, const hough_thresholds *th,
+                 hough_ctx **out)
+{
+    if (!out)
+        return HOUGH_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!geometry_ok(g) || !th || th->vote_threshold < 1 || th->assoc_tol_bins < 0 ||
+        th->max_peaks < 0)
+        return HOUGH_ERR_INVALID_ARG;
+    if (n_theta < 1 || n_theta > HOUGH_MAX_THETA || n_rho < 4 || n_rho > HOUGH_MAX_RHO ||
+        n_rho % 4 != 0 || th->max_peaks > HOUGH_MAX_PEAKS)
+        return HOUGH_ERR_UNSUPPORTED_SHAPE;
+    int dev = 0, ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        return HOUGH_ERR_NO_DEVICE;
+    }
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return HOUGH_ERR_NO_DEVICE;
+    hough_ctx *ctx = new (std::nothrow) hough_ctx();
+    if (!ctx)
+        return HOUGH_ERR_ALLOC;
+    ctx->device = dev;
+    ctx->g = *g;
+    ctx->th = *th;
+    ctx->n_theta = n_theta;
+    ctx->n_rho = n_rho;
+    ctx->C.resize(n_theta);
+    ctx->S.resize(n_theta);
+    int64_t D = 0;
+    int rc = hough_tables(g, n_theta, n_rho, ctx->C.data(), ctx->S.data(), &D);
+    if (rc != HOUGH_OK) {
+        delete ctx;
+        return rc;
+    }
+    ctx->D = D;
+    int smem_optin = 0;
+    if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess) {
+        delete ctx;
+        return HOUGH_ERR_CUDA;
+    }
+    // the kernel's static shared scalars share the per-block limit
+    ctx->smem_optin = (size_t)smem_optin - 64;
+    if (cudaMalloc(&ctx->d_C, sizeof(int32_t) * n_theta) != cudaSuccess ||
+        cudaMalloc(&ctx->d_S, sizeof(int32_t) * n_theta) != cudaSuccess) {
+        hough_destroy(ctx);
+        return HOUGH_ERR_ALLOC;
+    }
+    if (cudaMemcpy(ctx->d_C, ctx->C.data(), sizeof(int32_t) * n_theta, cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(ctx->d_S, ctx->S.data(), sizeof(int32_t) * n_theta, cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+        hough_destroy(ctx);
+        return HOUGH_ERR_CUDA;
+    }
+    hough_launch l{};
+    size_t smem = 0;
+    rc = resolve_launch(ctx, hough_launch{}, l, smem);
+    if (rc != HOUGH_OK) {
+        hough_destroy(ctx);
+        return rc;
+    }
+    ctx->launch = l;
+    *out = ctx;
+    return HOUGH_OK;
+}
+
+void hough_destroy(hough_ctx *ctx)
+{
+    if (!ctx)
+        return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(ctx->device);
+    for (auto &kv : ctx->counters)
+        cudaFree(kv.second);
+    cudaFree(ctx->d_C);
+    cudaFree(ctx->d_S);
+    cudaFree(ctx->stage_dev);
+    for (int i = 0; i < 2; ++i) {
+        if (ctx->host_streams[i])
+            cudaStreamDestroy(ctx->host_streams[i]);
+        if (ctx->host_events[i])
+            cudaEventDestroy(ctx->host_events[i]);
+    }
+    cudaSetDevice(prev);
+    delete ctx;
+}
+
+int hough_encode(hough_ctx *ctx, const int32_t *vane, const int32_t *strip, int64_t n,
+                 int32_t *phi_q, int32_t *z_q, void *stream)
+{
+    if (!ctx || n < 0 || (n > 0 && (!vane || !strip || !phi_q || !z_q)))
+        return fail(ctx, HOUGH_ERR_INVALID_ARG);
+    if (n == 0)
+        return HOUGH_OK;
+    const hough_geometry &g = ctx->g;
+    int blocks = (int)std::min<long long>((n + 255) / 256, (long long)ctx->num_sms * 8);
+    hk::encode_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(
+        vane, strip, n, (int)(360LL * g.phi_u_per_deg / g.n_vanes), g.z_min_u, g.z_pitch_u,
+        g.z_pitch_u / 2, phi_q, z_q);
+    if (cudaGetLastError() != cudaSuccess)
+        return fail(ctx, HOUGH_ERR_CUDA);
+    ctx->launches += 1;
+    return HOUGH_OK;
+}
+
+int hough_find(hough_ctx *ctx, const hough_hits *hits, const int64_t *window_offsets,
+               int64_t n_windows, const hough_tracks *tracks_out, void *stream)
+{
+    int rc = check_find_args(ctx, hits, window_offsets, n_windows, tracks_out);
+    if (rc != HOUGH_OK)
+        return fail(ctx, rc);
+    if (n_windows == 0)
+        return HOUGH_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned int *c = counter_for(ctx, s);
+    if (!c)
+        return fail(ctx, HOUGH_ERR_ALLOC);
+    rc = launch_find(ctx, hits, window_offsets, n_windows, tracks_out, s, c, ctx->launch);
+    return fail(ctx, rc);
+}
+
+int hough_find_host(hough_ctx *ctx, const hough_hits *hits, const int64_t *window_offsets,
+                    int64_t n_windows, const hough_tracks *out, void *stream)
+{
+    int rc = check_find_args(ctx, hits, window_offsets, n_windows, out);
+    if (rc != HOUGH_OK)
+        return fail(ctx, rc);
+    if (n_windows == 0)
+        return HOUGH_OK;
+    const long long H = hits->n_hits;
+    const bool raw = hits->vane && hits->strip;
+    const int mp = ctx->th.max_peaks;
+    const bool exp_acc = (ctx->th.flags & HOUGH_FLAG_EXPORT_ACC) != 0;
+    const size_t acc_per_w = exp_acc ? (size_t)ctx->n_theta * ctx->n_rho * 4 : 0;
+    // device layout: offsets | in0 | in1 | peaks | n_peaks | n_found | hit_track | track_hits | status | acc
+    auto al = [](size_t x) { return hk::align_up(x, 256); };
+    size_t o_off = 0;
+    size_t o_in0 = al(o_off + 8 * (size_t)(n_windows + 1));
+    size_t o_in1 = al(o_in0 + 4 * (size_t)H);
+    size_t o_pk = al(o_in1 + 4 * (size_t)H);
+    size_t o_np = al(o_pk + sizeof(hough_peak) * (size_t)n_windows * mp);
+    size_t o_nf = al(o_np + 4 * (size_t)n_windows);
+    size_t o_ht = al(o_nf + 4 * (size_t)n_windows);
+    size_t o_th = al(o_ht + 4 * (size_t)H);
+    size_t o_st = al(o_th + 4 * (size_t)H);
+    size_t o_acc = al(o_st + 4 * (size_t)n_windows);
+    size_t total = al(o_acc + acc_per_w * (size_t)n_windows);
+    if (total > ctx->stage_bytes) {
+        cudaFree(ctx->stage_dev);
+        ctx->stage_dev = nullptr;
+        ctx->stage_bytes = 0;
+        if (cudaMalloc(&ctx->stage_dev, total) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, HOUGH_ERR_ALLOC);
+        }
+        ctx->stage_bytes = total;
+    }
+    char *base = (char *)ctx->stage_dev;
+    cudaStream_t s = (cudaStream_t)stream;
+    auto cp = [&](void *dst, const void *src, size_t n, cudaMemcpyKind k) {
+        return n == 0 || cudaMemcpyAsync(dst, src, n, k, s) == cudaSuccess;
+    };
+    bool ok = cp(base + o_off, window_offsets, 8 * (size_t)(n_windows + 1), cudaMemcpyHostToDevice) &&
+              cp(base + o_in0, raw ? hits->vane : hits->phi_q, 4 * (size_t)H, cudaMemcpyHostToDevice) &&
+              cp(base + o_in1, raw ? hits->strip : hits->z_q, 4 * (size_t)H, cudaMemcpyHostToDevice);
+    if (!ok)
+        return fail(ctx, HOUGH_ERR_CUDA);
+    hough_hits dh{};
+    dh.n_hits = H;
+    if (raw) {
+        dh.vane = (const int32_t *)(base + o_in0);
+        dh.strip = (const int32_t *)(base + o_in1);
+    } else {
+        dh.phi_q = (const int32_t *)(base + o_in0);
+        dh.z_q = (const int32_t *)(base + o_in1);
+    }
+    hough_tracks dt{};
+    dt.peaks = (hough_peak *)(base + o_pk);
+    dt.n_peaks = (int32_t *)(base + o_np);
+    dt.n_found = (int32_t *)(base + o_nf);
+    dt.hit_track = (int32_t *)(base + o_ht);
+    dt.track_hits = (int32_t *)(base + o_th);
+    dt.window_status = (uint32_t *)(base + o_st);
+    dt.acc = exp_acc ? (int32_t *)(base + o_acc) : nullptr;
+    unsigned int *c = counter_for(ctx, s);
+    if (!c)
+        return fail(ctx, HOUGH_ERR_ALLOC);
+    rc = launch_find(ctx, &dh, (const int64_t *)(base + o_off), n_windows, &dt, s, c, ctx->launch);
+    if (rc != HOUGH_OK)
+        return fail(ctx, rc);
+    ok = cp(out->peaks, dt.peaks, sizeof(hough_peak) * (size_t)n_windows * mp, cudaMemcpyDeviceToHost) &&
+         cp(out->n_peaks, dt.n_peaks, 4 * (size_t)n_windows, cudaMemcpyDeviceToHost) &&
+         (!out->n_found || cp(out->n_found, dt.n_found, 4 * (size_t)n_windows, cudaMemcpyDeviceToHost)) &&
+         cp(out->hit_track, dt.hit_track, 4 * (size_t)H, cudaMemcpyDeviceToHost) &&
+         cp(out->track_hits, dt.track_hits, 4 * (size_t)H, cudaMemcpyDeviceToHost) &&
+         cp(out->window_status, dt.window_status, 4 * (size_t)n_windows, cudaMemcpyDeviceToHost) &&
+         (!exp_acc || cp(out->acc, dt.acc, acc_per_w * (size_t)n_windows, cudaMemcpyDeviceToHost));
+    if (!ok)
+        return fail(ctx, HOUGH_ERR_CUDA);
+    if (cudaStreamSynchronize(s) != cudaSuccess)
+        return fail(ctx, HOUGH_ERR_CUDA);
+    return HOUGH_OK;
+}
+
+int hough_plan_create(hough_ctx *ctx, const hough_hits *hits, const int64_t *window_offsets,
+                      int64_t n_windows, const hough_tracks *tracks_out, void *stream,
+                      hough_plan **out)
+{
+    if (!out)
+        return fail(ctx, HOUGH_ERR_INVALID_ARG);
+    *out = nullptr;
+    int rc = check_find_args(ctx, hits, window_offsets, n_windows, tracks_out);
+    if (rc != HOUGH_OK)
+        return fail(ctx, rc);
+    hough_plan *plan = new (std::nothrow) hough_plan();
+    if (!plan)
+        return fail(ctx, HOUGH_ERR_ALLOC);
+    plan->ctx = ctx;
+    if (cudaMalloc(&plan->counter, 2 * sizeof(unsigned int)) != cudaSuccess ||
+        cudaMemset(plan->counter, 0, 2 * sizeof(unsigned int)) != cudaSuccess) {
+        hough_plan_destroy(plan);
+        return fail(ctx, HOUGH_ERR_ALLOC);
+    }
+    cudaStream_t cap = nullptr;
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+        hough_plan_destroy(plan);
+        return fail(ctx, HOUGH_ERR_CUDA);
+    }
+    (void)stream;
+    Prepared pr{};
+    rc = n_windows > 0 ? prepare_find(ctx, n_windows, ctx->launch, pr) : HOUGH_OK;
+    if (rc != HOUGH_OK) {
+        // nothing to capture
+    } else if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        rc = HOUGH_ERR_CUDA;
+    } else {
+        if (n_windows > 0)
+            rc = enqueue_find(ctx, hits, window_offsets, n_windows, tracks_out, cap, plan->counter,
+                              pr);
+        if (cudaStreamEndCapture(cap, &plan->graph) != cudaSuccess && rc == HOUGH_OK)
+            rc = HOUGH_ERR_CUDA;
+    }
+    cudaStreamDestroy(cap);
+    if (rc == HOUGH_OK && cudaGraphInstantiate(&plan->exec, plan->graph, 0) != cudaSuccess)
+        rc = HOUGH_ERR_CUDA;
+    if (rc != HOUGH_OK) {
+        cudaGetLastError();
+        hough_plan_destroy(plan);
+        return fail(ctx, rc);
+    }
+    *out = plan;
+    return HOUGH_OK;
+}
+
+int hough_plan_launch(hough_plan *plan, void *stream)
+{
+    if (!plan || !plan->exec)
+        return HOUGH_ERR_INVALID_ARG;
+    if (cudaGraphLaunch(plan->exec, (cudaStream_t)stream) != cudaSuccess)
+        return fail(plan->ctx, HOUGH_ERR_CUDA);
+    plan->ctx->launches += 1;
+    return HOUGH_OK;
+}
+
+void hough_plan_destroy(hough_plan *plan)
+{
+    if (!plan)
+        return;
+    if (plan->exec)
+        cudaGraphExecDestroy(plan->exec);
+    if (plan->graph)
+        cudaGraphDestroy(plan->graph);
+    cudaFree(plan->counter);
+    delete plan;
+}
+
+int hough_get_launch(const hough_ctx *ctx, hough_launch *out)
+{
+    if (!ctx || !out)
+        return HOUGH_ERR_INVALID_ARG;
+    *out = ctx->launch;
+    return HOUGH_OK;
+}
+
+int hough_set_launch(hough_ctx *ctx, const hough_launch *cfg)
+{
+    if (!ctx || !cfg)
+        return fail(ctx, HOUGH_ERR_INVALID_ARG);
+    hough_launch l{};
+    size_t smem = 0;
+    int rc = resolve_launch(ctx, *cfg, l, smem);
+    if (rc != HOUGH_OK)
+        return fail(ctx, rc);
+    ctx->launch = l;
+    return HOUGH_OK;
+}
+
+int hough_autotune(hough_ctx *ctx, const hough_hits *hits, const int64_t *window_offsets,
+                   int64_t n_windows, const hough_tracks *tracks_out, void *stream, int iters,
+                   hough_launch *best)
+{
+    int rc = check_find_args(ctx, hits, window_offsets, n_windows, tracks_out);
+    if (rc != HOUGH_OK || iters < 1)
+        return fail(ctx, rc != HOUGH_OK ? rc : HOUGH_ERR_INVALID_ARG);
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned int *c = counter_for(ctx, s);
+    if (!c)
+        return fail(ctx, HOUGH_ERR_ALLOC);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return fail(ctx, HOUGH_ERR_CUDA);
+    hough_launch chosen = ctx->launch;
+    float best_ms = 1e30f;
+    for (int threads : {256, 512, 1024})
+        for (int wr : {32, 64, 128})
+            for (int cps : {1, 2})
+                for (int hs : {1024, 2048}) {
+                    hough_launch req{threads, wr, hs, cps};
+                    hough_launch l{};
+                    size_t smem = 0;
+                    if (resolve_launch(ctx, req, l, smem) != HOUGH_OK)
+                        continue;
+                    if (cps > 1 && smem * cps > ctx->smem_optin)
+                        continue;
+                    if (launch_find(ctx, hits, window_offsets, n_windows, tracks_out, s, c, l) !=
+                        HOUGH_OK) {
+                        cudaGetLastError();
+                        continue;
+                    }
+                    cudaEventRecord(e0, s);
+                    for (int i = 0; i < iters; ++i)
+                        launch_find(ctx, hits, window_offsets, n_windows, tracks_out, s, c, l);
+                    cudaEventRecord(e1, s);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) {
+                        cudaEventDestroy(e0);
+                        cudaEventDestroy(e1);
+                        return fail(ctx, HOUGH_ERR_CUDA);
+                    }
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        chosen = l;
+                    }
+                }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->launch = chosen;
+    // leave the outputs holding the chosen shape's (identical) results
+    rc = launch_find(ctx, hits, window_offsets, n_windows, tracks_out, s, c, chosen);
+    if (best)
+        *best = chosen;
+    return fail(ctx, rc);
+}
+
+const char *hough_status_string(int status)
+{
+    switch (status) {
+    case HOUGH_OK: return "HOUGH_OK";
+    case HOUGH_ERR_INVALID_ARG: return "HOUGH_ERR_INVALID_ARG";
+    case HOUGH_ERR_ALLOC: return "HOUGH_ERR_ALLOC";
+    case HOUGH_ERR_CUDA: return "HOUGH_ERR_CUDA";
+    case HOUGH_ERR_TIMEOUT: return "HOUGH_ERR_TIMEOUT";
+    case HOUGH_ERR_UNSUPPORTED_SHAPE: return "HOUGH_ERR_UNSUPPORTED_SHAPE";
+    case HOUGH_ERR_NO_DEVICE: return "HOUGH_ERR_NO_DEVICE";
+    default: return "HOUGH_ERR_UNKNOWN";
+    }
+}
+
+int hough_last_error(const hough_ctx *ctx) { return ctx ? ctx->last_error : HOUGH_ERR_INVALID_ARG; }
+
+int64_t hough_launch_count(const hough_ctx *ctx) { return ctx ? (int64_t)ctx->launches : 0; }
+
+}  // extern "C"

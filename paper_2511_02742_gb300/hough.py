@@ -1,0 +1,338 @@
+"""Python binding of libhough (include/hough.h): argument marshalling only.
+
+Every step of the path runs in the CUDA library; this module only converts
+torch tensors / numpy arrays to the C structs and pointers of the C ABI.  If
+the library has not been built, loading fails loudly: there is no fallback.
+
+The function names follow the C ABI (hough_create, hough_find, ...); the
+``Finder`` class bundles a context with output allocation for torch users.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+HOUGH_OK = 0
+HOUGH_FRAC_BITS = 24
+HOUGH_MAX_THETA = 4096
+HOUGH_MAX_RHO = 2048
+HOUGH_MAX_PEAKS = 256
+HOUGH_WIN_PEAK_OVERFLOW = 1
+HOUGH_WIN_HIT_OUT_OF_RANGE = 2
+HOUGH_WIN_VOTE_OUT_OF_RANGE = 4
+HOUGH_WIN_BAD_OFFSETS = 8
+HOUGH_FLAG_EXPORT_ACC = 1
+
+PEAK_DTYPE = np.dtype([("theta", "<u2"), ("rho", "<u2"), ("votes", "<i4"),
+                       ("n_hits", "<i4"), ("hit_begin", "<i4")])
+
+P = ctypes.c_void_p
+
+
+class hough_geometry(ctypes.Structure):
+    _fields_ = [("n_vanes", ctypes.c_int32), ("n_z_strips", ctypes.c_int32),
+                ("z_pitch_u", ctypes.c_int32), ("z_min_u", ctypes.c_int32),
+                ("phi_u_per_deg", ctypes.c_int32), ("z_u_per_mm", ctypes.c_int32),
+                ("rho_min", ctypes.c_double), ("rho_max", ctypes.c_double)]
+
+
+class hough_thresholds(ctypes.Structure):
+    _fields_ = [("vote_threshold", ctypes.c_int32), ("assoc_tol_bins", ctypes.c_int32),
+                ("max_peaks", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+class hough_hits(ctypes.Structure):
+    _fields_ = [("phi_q", P), ("z_q", P), ("vane", P), ("strip", P), ("n_hits", ctypes.c_int64)]
+
+
+class hough_tracks(ctypes.Structure):
+    _fields_ = [("peaks", P), ("n_peaks", P), ("n_found", P), ("hit_track", P),
+                ("track_hits", P), ("window_status", P), ("acc", P)]
+
+
+class hough_launch(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("word_rows", ctypes.c_int32),
+                ("hit_stage", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class HoughError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {status_string(code)} ({code})")
+        self.code = code
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libhough.so; raise if it is missing (no CPU fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise RuntimeError(f"CUDA library not built ({_build.LIB} missing); "
+                               "run `python -c 'import __graft_entry__ as g; g.build()'`")
+        _build.build()
+    lib = ctypes.CDLL(_build.LIB)
+    i32, i64 = ctypes.c_int, ctypes.c_int64
+    sig = {
+        "hough_tables": ([P, i32, i32, P, P, P], i32),
+        "hough_create": ([P, i32, i32, P, P], i32),
+        "hough_destroy": ([P], None),
+        "hough_encode": ([P, P, P, i64, P, P, P], i32),
+        "hough_find": ([P, P, P, i64, P, P], i32),
+        "hough_find_host": ([P, P, P, i64, P, P], i32),
+        "hough_plan_create": ([P, P, P, i64, P, P, P], i32),
+        "hough_plan_launch": ([P, P], i32),
+        "hough_plan_destroy": ([P], None),
+        "hough_get_launch": ([P, P], i32),
+        "hough_set_launch": ([P, P], i32),
+        "hough_autotune": ([P, P, P, i64, P, P, i32, P], i32),
+        "hough_status_string": ([i32], ctypes.c_char_p),
+        "hough_last_error": ([P], i32),
+        "hough_launch_count": ([P], i64),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def status_string(code: int) -> str:
+    try:
+        return load().hough_status_string(int(code)).decode()
+    except Exception:  # pragma: no cover - library missing
+        return "HOUGH_ERR"
+
+
+def _check(code: int, what: str):
+    if code != HOUGH_OK:
+        raise HoughError(code, what)
+
+
+def make_geometry(d: dict) -> hough_geometry:
+    return hough_geometry(d["n_vanes"], d["n_z_strips"], d["z_pitch_u"], d["z_min_u"],
+                          d["phi_u_per_deg"], d["z_u_per_mm"], float(d["rho_min"]),
+                          float(d["rho_max"]))
+
+
+def _ptr(x):
+    """Address of a torch tensor or numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    return x.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+# ----------------------------------------------------------- C-ABI functions
+
+def hough_tables(geometry: dict, n_theta: int, n_rho: int):
+    """Host-only fixed-point tables: (C int32[n_theta], S int32[n_theta], D)."""
+    lib = load()
+    g = make_geometry(geometry)
+    C = np.zeros(n_theta, np.int32)
+    S = np.zeros(n_theta, np.int32)
+    D = np.zeros(1, np.int64)
+    _check(lib.hough_tables(ctypes.byref(g), n_theta, n_rho, _ptr(C), _ptr(S), _ptr(D)),
+           "hough_tables")
+    return C, S, int(D[0])
+
+
+def hough_create(geometry: dict, n_theta: int, n_rho: int, vote_threshold=5, assoc_tol_bins=1,
+                 max_peaks=64, flags=0) -> ctypes.c_void_p:
+    lib = load()
+    g = make_geometry(geometry)
+    th = hough_thresholds(vote_threshold, assoc_tol_bins, max_peaks, flags)
+    ctx = ctypes.c_void_p()
+    _check(lib.hough_create(ctypes.byref(g), n_theta, n_rho, ctypes.byref(th), ctypes.byref(ctx)),
+           "hough_create")
+    return ctx
+
+
+def hough_destroy(ctx) -> None:
+    load().hough_destroy(ctx)
+
+
+def make_hits(phi_q=None, z_q=None, vane=None, strip=None, n_hits=None) -> hough_hits:
+    if n_hits is None:
+        n_hits = len(vane) if vane is not None else len(phi_q)
+    return hough_hits(_ptr(phi_q), _ptr(z_q), _ptr(vane), _ptr(strip), int(n_hits))
+
+
+def make_tracks(out: dict) -> hough_tracks:
+    return hough_tracks(_ptr(out.get("peaks")), _ptr(out["n_peaks"]), _ptr(out.get("n_found")),
+                        _ptr(out["hit_track"]), _ptr(out["track_hits"]),
+                        _ptr(out["window_status"]), _ptr(out.get("acc")))
+
+
+def hough_encode(ctx, vane, strip, phi_q, z_q, stream=None) -> None:
+    _check(load().hough_encode(ctx, _ptr(vane), _ptr(strip), len(vane), _ptr(phi_q), _ptr(z_q),
+                               _stream(stream)), "hough_encode")
+
+
+def hough_find(ctx, hits: hough_hits, window_offsets, n_windows: int, tracks_out: hough_tracks,
+               stream=None) -> None:
+    _check(load().hough_find(ctx, ctypes.byref(hits), _ptr(window_offsets), int(n_windows),
+                             ctypes.byref(tracks_out), _stream(stream)), "hough_find")
+
+
+def hough_find_host(ctx, hits: hough_hits, window_offsets, n_windows: int,
+                    tracks_out: hough_tracks, stream=None) -> None:
+    _check(load().hough_find_host(ctx, ctypes.byref(hits), _ptr(window_offsets), int(n_windows),
+                                  ctypes.byref(tracks_out), _stream(stream)), "hough_find_host")
+
+
+def hough_plan_create(ctx, hits: hough_hits, window_offsets, n_windows: int,
+                      tracks_out: hough_tracks, stream=None) -> ctypes.c_void_p:
+    plan = ctypes.c_void_p()
+    _check(load().hough_plan_create(ctx, ctypes.byref(hits), _ptr(window_offsets), int(n_windows),
+                                    ctypes.byref(tracks_out), _stream(stream), ctypes.byref(plan)),
+           "hough_plan_create")
+    return plan
+
+
+def hough_plan_launch(plan, stream=None) -> None:
+    _check(load().hough_plan_launch(plan, _stream(stream)), "hough_plan_launch")
+
+
+def hough_plan_destroy(plan) -> None:
+    load().hough_plan_destroy(plan)
+
+
+def hough_get_launch(ctx) -> dict:
+    l = hough_launch()
+    _check(load().hough_get_launch(ctx, ctypes.byref(l)), "hough_get_launch")
+    return l.as_dict()
+
+
+def hough_set_launch(ctx, threads=0, word_rows=0, hit_stage=0, ctas_per_sm=0) -> None:
+    l = hough_launch(threads, word_rows, hit_stage, ctas_per_sm)
+    _check(load().hough_set_launch(ctx, ctypes.byref(l)), "hough_set_launch")
+
+
+def hough_autotune(ctx, hits: hough_hits, window_offsets, n_windows: int,
+                   tracks_out: hough_tracks, iters=3, stream=None) -> dict:
+    l = hough_launch()
+    _check(load().hough_autotune(ctx, ctypes.byref(hits), _ptr(window_offsets), int(n_windows),
+                                 ctypes.byref(tracks_out), _stream(stream), int(iters),
+                                 ctypes.byref(l)), "hough_autotune")
+    return l.as_dict()
+
+
+def hough_last_error(ctx) -> int:
+    return int(load().hough_last_error(ctx))
+
+
+def hough_launch_count(ctx) -> int:
+    return int(load().hough_launch_count(ctx))
+
+
+# ------------------------------------------------------------ torch helper
+
+def decode_peaks(peaks_i32) -> np.ndarray:
+    """int32[..., 4] peak records (as written by the library) -> PEAK_DTYPE array."""
+    a = np.ascontiguousarray(peaks_i32.cpu().numpy() if hasattr(peaks_i32, "cpu") else peaks_i32,
+                             dtype=np.int32)
+    return a.view(PEAK_DTYPE).reshape(a.shape[:-1])
+
+
+class Finder:
+    """One context (accumulator shape + thresholds) on the current CUDA device."""
+
+    def __init__(self, n_theta: int, n_rho: int, geometry: dict | None = None, vote_threshold=5,
+                 assoc_tol_bins=1, max_peaks=64, export_acc=False):
+        from .synth import GEOMETRY
+        self.geometry = dict(GEOMETRY if geometry is None else geometry)
+        self.n_theta, self.n_rho = n_theta, n_rho
+        self.max_peaks = max_peaks
+        self.export_acc = export_acc
+        flags = HOUGH_FLAG_EXPORT_ACC if export_acc else 0
+        self.ctx = hough_create(self.geometry, n_theta, n_rho, vote_threshold, assoc_tol_bins,
+                                max_peaks, flags)
+
+    def close(self):
+        if self.ctx:
+            hough_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def alloc_outputs(self, n_windows: int, n_hits: int, device="cuda", pin=False) -> dict:
+        import torch
+        kw = dict(device=device)
+        if device == "cpu" and pin:
+            kw["pin_memory"] = True
+        out = dict(
+            peaks=torch.zeros((n_windows, max(self.max_peaks, 1), 4), dtype=torch.int32, **kw),
+            n_peaks=torch.zeros(n_windows, dtype=torch.int32, **kw),
+            n_found=torch.zeros(n_windows, dtype=torch.int32, **kw),
+            hit_track=torch.zeros(max(n_hits, 1), dtype=torch.int32, **kw),
+            track_hits=torch.zeros(max(n_hits, 1), dtype=torch.int32, **kw),
+            window_status=torch.zeros(n_windows, dtype=torch.int32, **kw),
+        )
+        if self.export_acc:
+            out["acc"] = torch.zeros((n_windows, self.n_theta, self.n_rho), dtype=torch.int32, **kw)
+        return out
+
+    @staticmethod
+    def hits_struct(hits: dict) -> hough_hits:
+        if "vane" in hits:
+            return make_hits(vane=hits["vane"], strip=hits["strip"], n_hits=hits["vane"].numel()
+                             if hasattr(hits["vane"], "numel") else len(hits["vane"]))
+        return make_hits(phi_q=hits["phi_q"], z_q=hits["z_q"], n_hits=hits["phi_q"].numel()
+                         if hasattr(hits["phi_q"], "numel") else len(hits["phi_q"]))
+
+    def find(self, hits: dict, offsets, out: dict | None = None, stream=None) -> dict:
+        n_windows = int(offsets.numel() if hasattr(offsets, "numel") else len(offsets)) - 1
+        hs = self.hits_struct(hits)
+        if out is None:
+            out = self.alloc_outputs(n_windows, hs.n_hits)
+        hough_find(self.ctx, hs, offsets, n_windows, make_tracks(out), stream)
+        return out
+
+    def find_host(self, hits: dict, offsets, out: dict | None = None, stream=None) -> dict:
+        """End-to-end form: host (ideally pinned) buffers in and out."""
+        n_windows = int(offsets.numel() if hasattr(offsets, "numel") else len(offsets)) - 1
+        hs = self.hits_struct(hits)
+        if out is None:
+            out = self.alloc_outputs(n_windows, hs.n_hits, device="cpu")
+        hough_find_host(self.ctx, hs, offsets, n_windows, make_tracks(out), stream)
+        return out
+
+    def plan(self, hits: dict, offsets, out: dict, stream=None):
+        n_windows = int(offsets.numel()) - 1
+        return hough_plan_create(self.ctx, self.hits_struct(hits), offsets, n_windows,
+                                 make_tracks(out), stream)
+
+    def autotune(self, hits: dict, offsets, out: dict, iters=3, stream=None) -> dict:
+        n_windows = int(offsets.numel()) - 1
+        return hough_autotune(self.ctx, self.hits_struct(hits), offsets, n_windows,
+                              make_tracks(out), iters, stream)

@@ -1,0 +1,296 @@
+"""Bit-exact parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Everything here is integer, so the bar is exact equality of the accumulator
+(export mode), the peak list, n_found, the window status, hit_track and
+track_hits.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_02742_gb300 import synth
+from parity_helpers import G, assert_batch_equal, assert_window_equal, gpu_run, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hough():
+    from paper_2511_02742_gb300 import hough as h
+    h.load()
+    return h
+
+
+def _finder(hough, n_theta, n_rho, **kw):
+    return hough.Finder(n_theta, n_rho, **kw)
+
+
+@pytest.mark.parametrize("raw", [True, False])
+def test_tiny_config_exact_with_accumulator(hough, raw):
+    """10 single-track windows, 256 x 256, accumulator exported."""
+    cfg = synth.WORKLOADS["tiny"]
+    w = synth.workload("tiny")
+    f = _finder(hough, cfg["n_theta"], cfg["n_rho"], export_acc=True)
+    g = gpu_run(f, w, raw=raw)
+    ref = oracle_run(w, cfg["n_theta"], cfg["n_rho"], export=True)
+    assert_batch_equal(g, ref, w, check_acc=True)
+    f.close()
+
+
+def test_plain_config_exact(hough):
+    """1000 windows x 5 tracks, 1% noise, 512 x 512: every window."""
+    cfg = synth.WORKLOADS["plain"]
+    w = synth.workload("plain")
+    f = _finder(hough, cfg["n_theta"], cfg["n_rho"])
+    g = gpu_run(f, w)
+    ref = oracle_run(w, cfg["n_theta"], cfg["n_rho"])
+    assert_batch_equal(g, ref, w)
+    f.close()
+
+
+def test_plain_config_accumulator_export(hough):
+    cfg = synth.WORKLOADS["plain"]
+    w = synth.workload("plain", n_windows=60, seed=1)
+    f = _finder(hough, cfg["n_theta"], cfg["n_rho"], export_acc=True)
+    g = gpu_run(f, w)
+    ref = oracle_run(w, cfg["n_theta"], cfg["n_rho"], export=True)
+    assert_batch_equal(g, ref, w, check_acc=True)
+    f.close()
+
+
+def test_high_pileup_sampled_windows(hough):
+    """40 tracks/window, 5% noise, ~1e3 hits, 1024 x 1024: 300 windows on the
+    GPU, 25 of them checked one by one against the oracle (accumulator too)."""
+    cfg = synth.WORKLOADS["high_pileup"]
+    w = synth.workload("high_pileup", n_windows=300)
+    f = _finder(hough, cfg["n_theta"], cfg["n_rho"], export_acc=True)
+    g = gpu_run(f, w)
+    ids = np.random.default_rng(0).choice(w.n_windows, 25, replace=False)
+    refs = oracle_run(w, cfg["n_theta"], cfg["n_rho"], export=True, ids=ids)
+    for k, r in zip(ids, refs):
+        assert_window_equal(g, int(k), r, w.window(int(k)), check_acc=True)
+    f.close()
+
+
+def test_uneven_batch_poisson(hough):
+    """Poisson(10) tracks per window clipped to [1, 40], 2% noise, 512 x 512."""
+    w = synth.generate(3000, ("poisson", 10, 1, 40), (100.0, 300.0), 0.02, seed=5)
+    f = _finder(hough, 512, 512)
+    g = gpu_run(f, w)
+    ref = oracle_run(w, 512, 512)
+    assert_batch_equal(g, ref, w)
+    f.close()
+
+
+@pytest.mark.parametrize("n_theta,n_rho", [(180, 1000), (97, 332), (33, 64), (1024, 256), (1, 4)])
+def test_other_shapes(hough, n_theta, n_rho):
+    """The paper's 180 x 1000 binning and ragged shapes (partial last tile)."""
+    w = synth.generate(40, ("poisson", 8, 1, 40), (100.0, 300.0), 0.05, seed=n_theta)
+    f = _finder(hough, n_theta, n_rho, export_acc=True)
+    g = gpu_run(f, w)
+    ref = oracle_run(w, n_theta, n_rho, export=True)
+    assert_batch_equal(g, ref, w, check_acc=True)
+    f.close()
+
+
+def _windows_from_arrays(parts):
+    """Windows from explicit (vane, strip) arrays."""
+    vane = np.concatenate([np.asarray(p[0], np.int32) for p in parts]) if parts else np.zeros(0, np.int32)
+    strip = np.concatenate([np.asarray(p[1], np.int32) for p in parts]) if parts else np.zeros(0, np.int32)
+    off = np.zeros(len(parts) + 1, np.int64)
+    off[1:] = np.cumsum([len(p[0]) for p in parts])
+    n = len(vane)
+    return synth.Windows(vane, strip, off, np.zeros(n, np.int32), np.zeros(n), np.zeros((0, 4)),
+                         np.zeros(len(parts) + 1, np.int64))
+
+
+def test_edge_cases(hough):
+    """Empty windows, all hits at one point, hits on bin edges (phi = z = 0 sits
+    on a rho edge in every row), out-of-range strip addresses, a window with
+    fewer hits than T."""
+    rng = np.random.default_rng(3)
+    parts = [
+        ([], []),
+        ([5] * 40, [1000] * 40),                         # all hits at one (phi, z)
+        ([0] * 12, [1024] * 12),                         # phi = 0, z at strip 1024 centre
+        ([0, 1, 2], [7, 8, 9]),                          # < T hits
+        ([40, 3, -1, 7, 7], [5, 2048, 0, -3, 100]),      # outside the detector box
+        (rng.integers(0, 40, 300), rng.integers(0, 2048, 300)),
+        ([], []),
+    ]
+    w = _windows_from_arrays(parts)
+    for shape in [(256, 256), (180, 1000)]:
+        f = _finder(hough, *shape, export_acc=True)
+        g = gpu_run(f, w)
+        ref = oracle_run(w, *shape, export=True)
+        assert_batch_equal(g, ref, w, check_acc=True)
+        f.close()
+
+
+def test_encoded_hits_on_rho_edges(hough):
+    """Encoded hits chosen so that many votes land exactly on a bin edge
+    (floor of an exact integer quotient) and on the rho range ends."""
+    phi = np.array([0, 0, 0, 36000, 71999, 1800, 0, 0], np.int32)
+    z = np.array([0, 38912, -38912, 0, 0, 19, 1, -1], np.int32)
+    import torch
+    f = _finder(hough, 360, 1000, export_acc=True)
+    hits = dict(phi_q=torch.from_numpy(phi).cuda(), z_q=torch.from_numpy(z).cuda())
+    off = torch.tensor([0, len(phi)], dtype=torch.int64, device="cuda")
+    out = f.find(hits, off)
+    torch.cuda.synchronize()
+    r = oracle.find_window(G, 360, 1000, phi, z)
+    np.testing.assert_array_equal(out["acc"][0].cpu().numpy(), r["acc"])
+    np.testing.assert_array_equal(out["hit_track"].cpu().numpy(), r["hit_track"])
+    f.close()
+
+
+def test_large_windows_multi_stage_and_wide_counters(hough):
+    """A window larger than one shared-memory hit stage (16-bit counters, the
+    hits streamed in stages) and one above 65535 hits (32-bit counters)."""
+    rng = np.random.default_rng(7)
+    parts = [(rng.integers(0, 40, 5000), rng.integers(0, 2048, 5000)),
+             (rng.integers(0, 40, 70000), rng.integers(0, 2048, 70000)),
+             (rng.integers(0, 40, 200), rng.integers(0, 2048, 200))]
+    # make the big windows hold real peaks: add a few exact lines
+    w = _windows_from_arrays(parts)
+    f = _finder(hough, 128, 256, export_acc=True, vote_threshold=40, max_peaks=32)
+    g = gpu_run(f, w)
+    ref = oracle_run(w, 128, 256, export=True, vote_threshold=40, max_peaks=32)
+    assert_batch_equal(g, ref, w, check_acc=True)
+    f.close()
+
+
+def test_peak_overflow_and_candidate_buffer_fallback(hough):
+    """T = 1 on dense random windows: thousands of local maxima per tile
+    overflow the candidate buffer and take the exact slice-by-slice path;
+    the kept list must still be the exact top max_peaks."""
+    rng = np.random.default_rng(11)
+    parts = [(rng.integers(0, 40, 2000), rng.integers(0, 2048, 2000)) for _ in range(3)]
+    w = _windows_from_arrays(parts)
+    for mp in (256, 7, 0):
+        f = _finder(hough, 256, 1024, vote_threshold=1, max_peaks=mp)
+        g = gpu_run(f, w)
+        ref = oracle_run(w, 256, 1024, vote_threshold=1, max_peaks=mp)
+        assert ref["n_found"].min() > 3000
+        assert_batch_equal(g, ref, w)
+        f.close()
+
+
+def test_bad_offsets_are_flagged_not_read(hough):
+    import torch
+    w = synth.generate(4, 3, (100.0, 300.0), 0.0, seed=1)
+    f = _finder(hough, 64, 64)
+    hits = dict(vane=torch.from_numpy(w.vane).cuda(), strip=torch.from_numpy(w.strip).cuda())
+    off = w.offsets.copy()
+    off[2] = off[1] - 1              # window 1 decreasing, window 2 starts before window 1 ends
+    off_bad = np.concatenate([off, [w.n_hits + 10]])   # window 4 runs past n_hits
+    offt = torch.from_numpy(off_bad).cuda()
+    out = f.find(hits, offt)
+    torch.cuda.synchronize()
+    st = out["window_status"].cpu().numpy()
+    assert st[1] & hough.HOUGH_WIN_BAD_OFFSETS
+    assert st[4] & hough.HOUGH_WIN_BAD_OFFSETS
+    assert not st[0] & hough.HOUGH_WIN_BAD_OFFSETS
+    f.close()
+
+
+def test_launch_shapes_identical(hough):
+    """Every launch shape gives the same bits (deterministic integer path)."""
+    w = synth.generate(300, ("poisson", 10, 1, 40), (100.0, 300.0), 0.02, seed=9)
+    f = _finder(hough, 512, 512)
+    base = gpu_run(f, w)
+    for threads in (256, 512, 1024):
+        for wr in (32, 64):
+            for hs in (256, 2048):
+                hough.hough_set_launch(f.ctx, threads, wr, hs, 1)
+                g = gpu_run(f, w)
+                for k in ("n_peaks", "n_found", "status", "hit_track", "track_hits"):
+                    np.testing.assert_array_equal(g[k], base[k], err_msg=f"{k} {threads} {wr} {hs}")
+                np.testing.assert_array_equal(g["peaks"], base["peaks"])
+    f.close()
+
+
+def test_alone_vs_batch_and_repeat(hough):
+    """A window gives the same result alone (one window per call) and inside a
+    batch, and a repeated run gives the same bits."""
+    import torch
+    w = synth.generate(50, ("poisson", 10, 1, 40), (100.0, 300.0), 0.02, seed=12)
+    f = _finder(hough, 512, 512)
+    a = gpu_run(f, w)
+    b = gpu_run(f, w)
+    for k in a:
+        np.testing.assert_array_equal(a[k], b[k])
+    hits = dict(vane=torch.from_numpy(w.vane).cuda(), strip=torch.from_numpy(w.strip).cuda())
+    offs = torch.from_numpy(w.offsets).cuda()
+    out = f.alloc_outputs(w.n_windows, w.n_hits)
+    for k in range(w.n_windows):
+        sub = {key: (v[k:k + 1] if key in ("peaks", "n_peaks", "n_found", "window_status") else v)
+               for key, v in out.items()}
+        hough.hough_find(f.ctx, f.hits_struct(hits), offs[k:k + 2], 1, hough.make_tracks(sub))
+    torch.cuda.synchronize()
+    from parity_helpers import to_numpy
+    c = to_numpy(out, w.n_hits)
+    for k in a:
+        np.testing.assert_array_equal(a[k], c[k], err_msg=k)
+    f.close()
+
+
+def test_plan_graph_and_host_entry_point(hough):
+    """The CUDA-graph plan and the host-buffer entry point give the same bits."""
+    import torch
+    w = synth.generate(500, ("poisson", 10, 1, 40), (100.0, 300.0), 0.02, seed=13)
+    f = _finder(hough, 512, 512)
+    a = gpu_run(f, w)
+    hits = dict(vane=torch.from_numpy(w.vane).cuda(), strip=torch.from_numpy(w.strip).cuda())
+    offs = torch.from_numpy(w.offsets).cuda()
+    out = f.alloc_outputs(w.n_windows, w.n_hits)
+    plan = f.plan(hits, offs, out)
+    for _ in range(3):
+        hough.hough_plan_launch(plan)
+    torch.cuda.synchronize()
+    from parity_helpers import to_numpy
+    b = to_numpy(out, w.n_hits)
+    for k in a:
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+    hough.hough_plan_destroy(plan)
+    hh = dict(vane=torch.from_numpy(w.vane).pin_memory(), strip=torch.from_numpy(w.strip).pin_memory())
+    oh = f.alloc_outputs(w.n_windows, w.n_hits, device="cpu", pin=True)
+    f.find_host(hh, torch.from_numpy(w.offsets), out=oh)
+    c = to_numpy(oh, w.n_hits)
+    for k in a:
+        np.testing.assert_array_equal(a[k], c[k], err_msg=k)
+    f.close()
+
+
+def test_autotune_keeps_results(hough):
+    import torch
+    w = synth.generate(400, ("poisson", 10, 1, 40), (100.0, 300.0), 0.02, seed=14)
+    f = _finder(hough, 512, 512)
+    a = gpu_run(f, w)
+    hits = dict(vane=torch.from_numpy(w.vane).cuda(), strip=torch.from_numpy(w.strip).cuda())
+    offs = torch.from_numpy(w.offsets).cuda()
+    out = f.alloc_outputs(w.n_windows, w.n_hits)
+    best = f.autotune(hits, offs, out, iters=1)
+    torch.cuda.synchronize()
+    assert best["threads"] in (256, 512, 1024)
+    from parity_helpers import to_numpy
+    b = to_numpy(out, w.n_hits)
+    for k in a:
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+    f.close()
+
+
+def test_encode_entry_point(hough):
+    import torch
+    w = synth.generate(20, 5, (100.0, 300.0), 0.05, seed=2)
+    f = _finder(hough, 64, 64)
+    vane = torch.from_numpy(np.concatenate([w.vane, [40, -1]]).astype(np.int32)).cuda()
+    strip = torch.from_numpy(np.concatenate([w.strip, [2048, -5]]).astype(np.int32)).cuda()
+    phi = torch.empty_like(vane)
+    z = torch.empty_like(vane)
+    hough.hough_encode(f.ctx, vane, strip, phi, z)
+    torch.cuda.synchronize()
+    rp, rz = oracle.encode(G, vane.cpu().numpy(), strip.cpu().numpy())
+    np.testing.assert_array_equal(phi.cpu().numpy(), rp)
+    np.testing.assert_array_equal(z.cpu().numpy(), rz)
+    f.close()

@@ -1,0 +1,109 @@
+"""The C-ABI library builds, loads and exports every declared symbol; its
+host-only parts behave as documented.  No kernel runs here (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_02742_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+G = synth.GEOMETRY
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2511_02742_gb300 import build, hough
+    build.build()
+    return hough.load()
+
+
+def declared_functions():
+    names = []
+    inc = os.path.join(ROOT, "include")
+    for fn in sorted(os.listdir(inc)):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(inc, fn)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^[A-Za-z_][\w \*]*?\b(hough_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15, names
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in include/ but not exported"
+
+
+def test_tables_equal_oracle_tables(lib):
+    """The library's fixed-point tables (built on the host) equal the oracle's,
+    which are computed by independent code from the same definition."""
+    from paper_2511_02742_gb300 import hough
+    for n_theta, n_rho in [(180, 1000), (256, 256), (512, 512), (1024, 1024), (97, 332), (1, 4)]:
+        C, S, D = hough.hough_tables(G, n_theta, n_rho)
+        oc, os_, od = oracle.tables(G, n_theta, n_rho)
+        np.testing.assert_array_equal(C, oc)
+        np.testing.assert_array_equal(S, os_)
+        assert D == od
+    geom = dict(G, rho_min=-123.5, rho_max=321.25, phi_u_per_deg=100)
+    C, S, D = hough.hough_tables(geom, 77, 444)
+    oc, os_, od = oracle.tables(geom, 77, 444)
+    np.testing.assert_array_equal(C, oc)
+    np.testing.assert_array_equal(S, os_)
+    assert D == od
+
+
+def test_status_strings(lib):
+    from paper_2511_02742_gb300 import hough
+    assert hough.status_string(0) == "HOUGH_OK"
+    assert hough.status_string(-1) == "HOUGH_ERR_INVALID_ARG"
+    assert hough.status_string(-5) == "HOUGH_ERR_UNSUPPORTED_SHAPE"
+    assert hough.status_string(12345) == "HOUGH_ERR_UNKNOWN"
+
+
+def test_create_rejects_bad_arguments_before_touching_a_device(lib):
+    from paper_2511_02742_gb300 import hough
+    bad = [
+        (dict(G, n_vanes=0), 64, 64, {}),
+        (dict(G, rho_max=-600.0), 64, 64, {}),
+        (G, 64, 64, dict(vote_threshold=0)),
+        (G, 64, 64, dict(assoc_tol_bins=-1)),
+        (G, 64, 64, dict(max_peaks=-3)),
+    ]
+    for geom, nt, nr, kw in bad:
+        with pytest.raises(hough.HoughError) as e:
+            hough.hough_create(geom, nt, nr, **kw)
+        assert e.value.code == -1
+    for nt, nr, kw in [(0, 64, {}), (64, 6, {}), (64, 4096, {}), (8192, 64, {}),
+                       (64, 64, dict(max_peaks=257))]:
+        with pytest.raises(hough.HoughError) as e:
+            hough.hough_create(G, nt, nr, **kw)
+        assert e.value.code == -5
+
+
+def test_null_pointers_are_rejected(lib):
+    assert lib.hough_create(None, 64, 64, None, None) == -1
+    assert lib.hough_find(None, None, None, 0, None, None) == -1
+    assert lib.hough_plan_launch(None, None) == -1
+    lib.hough_destroy(None)
+    lib.hough_plan_destroy(None)
+    assert lib.hough_last_error(None) == -1
+    assert lib.hough_launch_count(None) == 0
+    C = np.zeros(4, np.int32)
+    assert lib.hough_tables(None, 4, 4, C.ctypes.data_as(ctypes.c_void_p), None, None) == -1
+
+
+def test_no_device_is_reported_not_faked(lib):
+    """Without a GPU the library says so; it never computes on the CPU."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2511_02742_gb300 import hough
+    with pytest.raises(hough.HoughError) as e:
+        hough.hough_create(G, 64, 64)
+    assert e.value.code == -6
