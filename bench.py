@@ -1,0 +1,401 @@
+"""Benchmark of the track-finding path on GB300.
+
+Workload (default): 1e5 time windows with Poisson(10) tracks clipped to
+[1, 40], 2% noise hits, 512 x 512 accumulator -- the batched configuration.
+One step = one pass of the whole path (hit encoding from strip addresses,
+Hough voting, peak extraction, association and per-peak compaction) over the
+whole batch, as one persistent kernel replayed from a CUDA graph.
+
+Prints one JSON line (rank 0).  Timing: W untimed warm-up steps, then K timed
+steps, each bracketed by CUDA events on the launching stream with L2 flushed
+(a 512 MB write) between steps; barrier + synchronize around the timed region;
+max over ranks.  Under torchrun each rank runs its own replica with its own
+windows (weak scaling, no collective on the data path).
+
+--impl reference times the CPU oracle (the plain C definition of the path) on
+the same workload, on the host cores, as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "track-finding windows/s batched vs plain, bit-exact to oracle; p50/p99 latency"
+UNIT = "windows/s"
+
+
+def _env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def _workload(name, n_windows, seed):
+    from paper_2511_02742_gb300 import synth
+    return synth.workload(name, n_windows=n_windows, seed=seed)
+
+
+def _workload_desc(name, n_windows):
+    from paper_2511_02742_gb300 import synth
+    cfg = synth.WORKLOADS[name]
+    return (f"{name}: {n_windows} windows, tracks/window {cfg['tracks']}, p {cfg['p_range']} MeV/c, "
+            f"{int(cfg['noise_frac'] * 100)}% noise, {cfg['n_theta']}x{cfg['n_rho']} int32 "
+            f"accumulator (uint8/uint16 packed in shared memory), T=5, tol=1 bin, max_peaks=64")
+
+
+class ClockSampler:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in open(self.path):
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def _oracle_windows_per_s(w, n_theta, n_rho, n_sample, threads):
+    """Oracle (plain C, one window at a time) over the first n_sample windows."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_2511_02742_gb300 import synth
+    sub = w.subset(np.arange(min(n_sample, w.n_windows)))
+    phi, z = oracle.encode(synth.GEOMETRY, sub.vane, sub.strip)
+    chunks = np.array_split(np.arange(sub.n_windows), threads)
+
+    def run(ids):
+        if len(ids) == 0:
+            return
+        a, b = int(sub.offsets[ids[0]]), int(sub.offsets[ids[-1] + 1])
+        oracle.find_batch(synth.GEOMETRY, n_theta, n_rho, phi[a:b], z[a:b],
+                          sub.offsets[ids[0]:ids[-1] + 2] - a)
+
+    t0 = time.perf_counter()
+    if threads == 1:
+        run(chunks[0])
+    else:
+        with ThreadPoolExecutor(threads) as ex:
+            list(ex.map(run, chunks))
+    dt = time.perf_counter() - t0
+    return sub.n_windows / dt, dt, sub.n_windows
+
+
+def _cpu_baseline(w, n_theta, n_rho, budget_s=12.0):
+    """Single-thread and all-cores oracle rates on a bounded sample."""
+    probe, dt, n = _oracle_windows_per_s(w, n_theta, n_rho, 200, 1)
+    n1 = int(max(200, min(w.n_windows, probe * budget_s)))
+    v1, dt1, n1 = _oracle_windows_per_s(w, n_theta, n_rho, n1, 1)
+    cores = os.cpu_count() or 1
+    vN, dtN, nN = _oracle_windows_per_s(w, n_theta, n_rho, min(w.n_windows, n1 * cores // 2), cores)
+    return {"value": round(vN, 2), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {nN} windows of the same workload, windows split over {cores} threads "
+                      f"({dtN:.1f} s)",
+            "value_single_core": round(v1, 2),
+            "sample_single_core": f"first {n1} windows, 1 thread ({dt1:.1f} s)"}
+
+
+def run_reference(args):
+    rank, local_rank, world = _env_rank()
+    if rank != 0:
+        return 0
+    from paper_2511_02742_gb300 import synth
+    cfg = synth.WORKLOADS[args.workload]
+    n_windows = args.windows or cfg["n_windows"]
+    w = _workload(args.workload, n_windows, 0)
+    cores = os.cpu_count() or 1
+    probe, _, _ = _oracle_windows_per_s(w, cfg["n_theta"], cfg["n_rho"], 200, 1)
+    per_step = int(max(cores, min(w.n_windows, probe * cores * 0.5 * 4)))   # ~4 s per step
+    for _ in range(args.warmup):
+        _oracle_windows_per_s(w, cfg["n_theta"], cfg["n_rho"], min(per_step, 2 * cores), cores)
+    times = []
+    for _ in range(args.steps):
+        v, dt, n = _oracle_windows_per_s(w, cfg["n_theta"], cfg["n_rho"], per_step, cores)
+        times.append(dt)
+    total = per_step * args.steps / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(total, 2), "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * sum(times) / len(times), 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": _workload_desc(args.workload, n_windows)},
+        "cpu_baseline": {"value": round(total, 2), "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"first {per_step} windows per step, {cores} threads"},
+        "e2e": {"value": round(total, 2), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _flush_l2(buf):
+    buf.add_(1)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2511_02742_gb300 import hough, synth
+
+    rank, local_rank, world = _env_rank()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    cfg = synth.WORKLOADS[args.workload]
+    n_theta, n_rho = cfg["n_theta"], cfg["n_rho"]
+    n_windows = args.windows or cfg["n_windows"]
+    t_gen = time.time()
+    w = _workload(args.workload, n_windows, 1000 * rank)      # each replica its own windows
+    t_gen = time.time() - t_gen
+
+    f = hough.Finder(n_theta, n_rho)
+    vane = torch.from_numpy(w.vane).to(dev)
+    strip = torch.from_numpy(w.strip).to(dev)
+    offs = torch.from_numpy(w.offsets).to(dev)
+    hits = dict(vane=vane, strip=strip)
+    out = f.alloc_outputs(w.n_windows, w.n_hits, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    launch = hough.hough_get_launch(f.ctx)
+    if args.autotune:
+        sub = w.subset(np.arange(min(w.n_windows, 20000)))
+        sh = dict(vane=torch.from_numpy(sub.vane).to(dev), strip=torch.from_numpy(sub.strip).to(dev))
+        so = torch.from_numpy(sub.offsets).to(dev)
+        souts = f.alloc_outputs(sub.n_windows, sub.n_hits, device=dev)
+        launch = f.autotune(sh, so, souts, iters=2)
+        del sh, so, souts
+    plan = f.plan(hits, offs, out)
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)   # 512 MB > L2
+
+    for _ in range(max(args.warmup, 0)):
+        hough.hough_plan_launch(plan, stream)
+    torch.cuda.synchronize()
+
+    n0 = hough.hough_launch_count(f.ctx)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            _flush_l2(flush)
+            ev[i][0].record(stream)
+            hough.hough_plan_launch(plan, stream)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    n_launch = hough.hough_launch_count(f.ctx) - n0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(step_ms) / len(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    value = world * w.n_windows / (ms * 1e-3)
+
+    # algorithmic work per launch
+    lens = np.diff(w.offsets)
+    valid = ((w.vane >= 0) & (w.vane < synth.N_VANES) & (w.strip >= 0) &
+             (w.strip < synth.N_Z_STRIPS))
+    n_valid = int(valid.sum())
+    votes = n_valid * n_theta
+    n_peaks = out["n_peaks"].sum().item()
+    algo_bytes = (8 * w.n_hits + 8 * (w.n_windows + 1) + 8 * w.n_hits + 16 * n_peaks
+                  + 12 * w.n_windows)
+
+    result = {}
+    if rank == 0:
+        # ---- plain form: one window per launch, no graph, same kernel
+        n_plain = min(w.n_windows, args.plain_windows)
+        tracks = out
+        sub_struct = f.hits_struct(hits)
+        torch.cuda.synchronize()
+        for k in range(min(50, n_plain)):   # warm-up
+            sub = {key: (v[k:k + 1] if key in ("peaks", "n_peaks", "n_found", "window_status") else v)
+                   for key, v in tracks.items()}
+            hough.hough_find(f.ctx, sub_struct, offs[k:k + 2], 1, hough.make_tracks(sub), stream)
+        torch.cuda.synchronize()
+        subs = [hough.make_tracks({key: (v[k:k + 1] if key in ("peaks", "n_peaks", "n_found",
+                                                                "window_status") else v)
+                                   for key, v in tracks.items()}) for k in range(n_plain)]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(n_plain):
+            hough.hough_find(f.ctx, sub_struct, offs[k:k + 2], 1, subs[k], stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms = e0.elapsed_time(e1)
+        plain_value = n_plain / (plain_ms * 1e-3)
+
+        # ---- e2e through the host-buffer entry point (pinned host memory)
+        hv = torch.from_numpy(w.vane).pin_memory()
+        hs = torch.from_numpy(w.strip).pin_memory()
+        ho = torch.from_numpy(w.offsets).pin_memory()
+        hout = f.alloc_outputs(w.n_windows, w.n_hits, device="cpu", pin=True)
+        f.find_host(dict(vane=hv, strip=hs), ho, out=hout)     # warm-up (grows staging)
+        e2e_steps = max(1, min(args.steps, 5))
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            f.find_host(dict(vane=hv, strip=hs), ho, out=hout)
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        h2d = 8 * w.n_hits + 8 * (w.n_windows + 1)
+        d2h = 16 * 64 * w.n_windows + 12 * w.n_windows + 8 * w.n_hits
+        # parity of the timed results against the oracle on a sample
+        import oracle
+        ids = np.random.default_rng(1).choice(w.n_windows, 40, replace=False)
+        phi, z = oracle.encode(synth.GEOMETRY, w.vane, w.strip)
+        pk = hough.decode_peaks(out["peaks"])
+        npk = out["n_peaks"].cpu().numpy()
+        ht = out["hit_track"].cpu().numpy()
+        mism = 0
+        for k in ids:
+            sl = w.window(int(k))
+            r = oracle.find_window(synth.GEOMETRY, n_theta, n_rho, phi[sl], z[sl])
+            if (npk[k] != r["n_peaks"] or not np.array_equal(pk[k][:r["n_peaks"]], r["peaks"])
+                    or not np.array_equal(ht[sl], r["hit_track"])):
+                mism += 1
+        cpu = _cpu_baseline(w, n_theta, n_rho, budget_s=args.cpu_budget) if args.cpu_budget > 0 \
+            else None
+        ach_votes = votes / (ms * 1e-3)
+        peaks_meas = {}
+        pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        if os.path.exists(pp):
+            peaks_meas = json.load(open(pp))
+        smem_peak = _smem_atomic_peak_gops(args)
+        result = {
+            "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": _workload_desc(args.workload, n_windows),
+                       "windows_per_gpu": w.n_windows, "hits_per_gpu": w.n_hits,
+                       "mean_hits_per_window": round(float(lens.mean()), 2),
+                       "l2": "flushed between steps (512 MB write)", "launch": launch,
+                       "parallelism": f"replicas x{world} (windows sharded, no collective)",
+                       "step": "one CUDA-graph replay of the persistent find kernel"},
+            "roofline": {"bound": "alu", "achieved": round(ach_votes / 1e9, 2),
+                         "peak": smem_peak["value"], "unit": "Gvote/s",
+                         "frac": round(ach_votes / 1e9 / smem_peak["value"], 4)
+                         if smem_peak["value"] else None,
+                         "traffic": None, "peak_source": smem_peak["source"],
+                         "algorithmic": f"{votes} shared-memory vote atomics per launch "
+                                        f"(valid hits x n_theta)",
+                         "hbm": {"achieved_gbs": round(algo_bytes / (ms * 1e-3) / 1e9, 2),
+                                 "peak_gbs": peaks_meas.get("hbm_gbs"),
+                                 "frac": round(algo_bytes / (ms * 1e-3) / 1e9 /
+                                               peaks_meas["hbm_gbs"], 4)
+                                 if peaks_meas.get("hbm_gbs") else None,
+                                 "algorithmic_bytes": algo_bytes}},
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(w.n_windows / e2e_s, 2), "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "entry_point": "hough_find_host (pinned host buffers)"},
+            "gpu_launches": int(n_launch),
+            "clocks": clk.summary(),
+            "plain": {"windows_per_s": round(plain_value, 2), "windows": n_plain,
+                      "form": "hough_find, one window per launch, no graph, same kernel",
+                      "batched_over_plain": round(value / world / plain_value, 2)},
+            "parity_sample": {"windows": len(ids), "mismatches": mism},
+            "wall_s_timed_region": round(t_wall, 4),
+            "generation_s": round(t_gen, 2),
+        }
+        print(json.dumps(result), flush=True)
+    hough.hough_plan_destroy(plan)
+    f.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def _smem_atomic_peak_gops(args):
+    """Shared-memory atomic throughput measured by the probe kernel (conflict-free
+    32-bit atomicAdd, all SMs), or the unit-count figure if the probe is off."""
+    nominal = 152 * 32 * 2.070   # SMs x banks x GHz: one 32-lane wavefront per clock per SM
+    if args.no_probe:
+        return {"value": round(nominal, 1), "source": "nominal: 152 SMs x 32 banks x 2.07 GHz"}
+    try:
+        from paper_2511_02742_gb300 import probe
+        v = probe.smem_atomic_gops()
+        return {"value": round(v, 1), "source": "measured: conflict-free smem atomicAdd probe"}
+    except Exception as e:  # pragma: no cover
+        return {"value": round(nominal, 1), "source": f"nominal (probe failed: {e})"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batched")
+    ap.add_argument("--windows", type=int, default=0)
+    ap.add_argument("--plain-windows", type=int, default=3000)
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-probe", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

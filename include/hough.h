@@ -39,7 +39,7 @@ extern "C" {
 
 /* Largest accumulator sides and peak list the kernels accept. */
 #define HOUGH_MAX_THETA 4096
-#define HOUGH_MAX_RHO 2048
+#define HOUGH_MAX_RHO 1024
 #define HOUGH_MAX_PEAKS 256
 
 typedef enum hough_status {

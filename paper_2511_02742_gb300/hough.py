@@ -19,7 +19,7 @@ from . import build as _build
 HOUGH_OK = 0
 HOUGH_FRAC_BITS = 24
 HOUGH_MAX_THETA = 4096
-HOUGH_MAX_RHO = 2048
+HOUGH_MAX_RHO = 1024
 HOUGH_MAX_PEAKS = 256
 HOUGH_WIN_PEAK_OVERFLOW = 1
 HOUGH_WIN_HIT_OUT_OF_RANGE = 2

@@ -79,7 +79,7 @@ def test_create_rejects_bad_arguments_before_touching_a_device(lib):
         with pytest.raises(hough.HoughError) as e:
             hough.hough_create(geom, nt, nr, **kw)
         assert e.value.code == -1
-    for nt, nr, kw in [(0, 64, {}), (64, 6, {}), (64, 4096, {}), (8192, 64, {}),
+    for nt, nr, kw in [(0, 64, {}), (64, 6, {}), (64, 2048, {}), (8192, 64, {}),
                        (64, 64, dict(max_peaks=257))]:
         with pytest.raises(hough.HoughError) as e:
             hough.hough_create(G, nt, nr, **kw)
