@@ -283,7 +283,7 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
         plain_ms = e0.elapsed_time(e1)
-        plain_value = n_plain / (plain_ms * 1e-3)
+        plain_value = n_plain / (plain_ms * 1e-3) if n_plain > 0 else None
 
         # ---- e2e through the host-buffer entry point (pinned host memory)
         hv = torch.from_numpy(w.vane).pin_memory()
@@ -350,9 +350,11 @@ def run_ours(args):
                     "entry_point": "hough_find_host (pinned host buffers)"},
             "gpu_launches": int(n_launch),
             "clocks": clk.summary(),
-            "plain": {"windows_per_s": round(plain_value, 2), "windows": n_plain,
+            "plain": {"windows_per_s": round(plain_value, 2) if plain_value else None,
+                      "windows": n_plain,
                       "form": "hough_find, one window per launch, no graph, same kernel",
-                      "batched_over_plain": round(value / world / plain_value, 2)},
+                      "batched_over_plain": round(value / world / plain_value, 2)
+                      if plain_value else None},
             "parity_sample": {"windows": len(ids), "mismatches": mism},
             "wall_s_timed_region": round(t_wall, 4),
             "generation_s": round(t_gen, 2),

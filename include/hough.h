@@ -34,8 +34,8 @@
 extern "C" {
 #endif
 
-/* Fraction bits of the fixed-point cos/sin tables (see hough_tables). */
-#define HOUGH_FRAC_BITS 24
+/* Largest scale exponent of the fixed-point cos/sin tables (see hough_tables). */
+#define HOUGH_MAX_FRAC_BITS 24
 
 /* Largest accumulator sides and peak list the kernels accept. */
 #define HOUGH_MAX_THETA 4096
@@ -161,15 +161,19 @@ typedef struct hough_plan hough_plan;
 /*
  * Fixed-point tables of Eq. (1) with the Section 5 binning, host only (no GPU).
  * theta_t = (t + 1/2) * 180/n_theta degrees; with span = rho_max - rho_min,
- *   C[t] = round(cos(theta_t) * 2^24 * n_rho / (span * phi_u_per_deg))
- *   S[t] = round(sin(theta_t) * 2^24 * n_rho / (span * z_u_per_mm))
- *   D    = round(-rho_min * 2^24 * n_rho / span)
- * rounding half away from zero.  A valid hit (phi, z) votes in row t for bin
- *   b = floor((phi*C[t] + z*S[t] + D) / 2^24)   (64-bit arithmetic),
- * if 0 <= b < n_rho.  C and S are host arrays of n_theta entries.
+ *   C[t] = round(cos(theta_t) * 2^K * n_rho / (span * phi_u_per_deg))
+ *   S[t] = round(sin(theta_t) * 2^K * n_rho / (span * z_u_per_mm))
+ *   D    = round(-rho_min * 2^K * n_rho / span)
+ * rounding half away from zero (computed in double precision), where K is
+ * the largest value <= HOUGH_MAX_FRAC_BITS for which |phi*C[t] + z*S[t] + D|
+ * < 2^31 at the four corners of the detector box for every t (so the sum is
+ * a 32-bit integer for every hit of the box).  A valid hit (phi, z) votes in
+ * row t for the bin b = floor((phi*C[t] + z*S[t] + D) / 2^K) if 0 <= b < n_rho.
+ * C and S are host arrays of n_theta entries; *D and *K receive the offset
+ * and the exponent.  Errors: INVALID_ARG, UNSUPPORTED_SHAPE (no K >= 8 fits).
  */
 int hough_tables(const hough_geometry *g, int n_theta, int n_rho, int32_t *C, int32_t *S,
-                 int64_t *D);
+                 int64_t *D, int32_t *K);
 
 /*
  * Create a context on the current CUDA device for one accumulator shape

@@ -97,16 +97,17 @@ def make_thresholds(vote_threshold=5, assoc_tol_bins=1, max_peaks=64, flags=0) -
 
 
 def tables(geom: dict, n_theta: int, n_rho: int):
-    """(C int32[n_theta], S int32[n_theta], D int) fixed-point tables."""
+    """(C int32[n_theta], S int32[n_theta], D int, K int): fixed-point tables
+    at scale 2^K (K the largest <= 24 keeping every box hit's sum in int32)."""
     lib = _load()
     g = make_geometry(geom)
     C = np.zeros(n_theta, np.int32)
     S = np.zeros(n_theta, np.int32)
     D = np.zeros(1, np.int64)
-    rc = lib.oracle_tables(ctypes.byref(g), n_theta, n_rho, _ptr(C), _ptr(S), _ptr(D))
-    if rc != 0:
+    k = lib.oracle_tables(ctypes.byref(g), n_theta, n_rho, _ptr(C), _ptr(S), _ptr(D))
+    if k < 0:
         raise ValueError("bad geometry or shape")
-    return C, S, int(D[0])
+    return C, S, int(D[0]), int(k)
 
 
 def encode(geom: dict, vane, strip):

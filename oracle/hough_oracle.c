@@ -14,8 +14,10 @@
  *      vanes, Section 2) and z at the centre of strip j, both in fixed-point
  *      units of 1/200 degree and 1/200 mm;
  *   B. Hough voting: every hit votes once in each theta row t for the rho bin
- *      b = floor((phi*C[t] + z*S[t] + D) / 2^24); votes outside [0, n_rho)
- *      are dropped and counted (Section 4 Eq. (1); Section 5 binning);
+ *      b = floor((phi*C[t] + z*S[t] + D) / 2^K); votes outside [0, n_rho)
+ *      are dropped and counted (Section 4 Eq. (1); Section 5 binning); the
+ *      scale 2^K is the largest (K <= 24) that keeps phi*C + z*S + D within
+ *      32-bit signed range for every hit of the detector box;
  *   C. peaks: every bin with count >= T that is a 3x3 local maximum under the
  *      row-major tie-break, sorted by (votes desc, theta asc, rho asc), the
  *      first max_peaks kept (Section 4 and Section 5, "the bin with the highest
@@ -38,7 +40,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define ORACLE_FRAC_BITS 24
+#define ORACLE_MAX_FRAC_BITS 24
 
 /* Same field order as the library's geometry struct; declared here on its own. */
 typedef struct {
@@ -100,17 +102,19 @@ static int64_t floor_div(int64_t num, int64_t den)
  * theta_t = (t + 1/2) * pi / n_theta (bin centres over 0..180 degrees).
  * One rho bin is (rho_max - rho_min)/n_rho; a hit's rho in bins, measured
  * from rho_min, is (phi/u_phi*cos + z/u_z*sin - rho_min) * n_rho/(rho_max - rho_min).
- * The tables hold those factors scaled by 2^24 and rounded half away from zero:
- *   C[t] = round(cos(theta_t) * 2^24 * n_rho / ((rho_max - rho_min) * u_phi))
- *   S[t] = round(sin(theta_t) * 2^24 * n_rho / ((rho_max - rho_min) * u_z))
- *   D    = round(-rho_min * 2^24 * n_rho / (rho_max - rho_min))
+ * The tables hold those factors scaled by 2^K and rounded half away from zero:
+ *   C[t] = round(cos(theta_t) * 2^K * n_rho / ((rho_max - rho_min) * u_phi))
+ *   S[t] = round(sin(theta_t) * 2^K * n_rho / ((rho_max - rho_min) * u_z))
+ *   D    = round(-rho_min * 2^K * n_rho / (rho_max - rho_min))
+ * K is the largest value <= 24 for which |phi*C[t] + z*S[t] + D| < 2^31 at the
+ * four corners of the detector box (phi in [0, 360 deg), z in [z_min, z_end])
+ * for every t; the sum is linear in (phi, z), so the whole box then fits.
+ * Returns K, or -1 on bad arguments or when no K >= 8 fits.
  */
-int oracle_tables(const oracle_geometry *g, int n_theta, int n_rho, int32_t *C, int32_t *S,
-                  int64_t *D)
+static void tables_at(const oracle_geometry *g, int n_theta, int n_rho, int k, int32_t *C,
+                      int32_t *S, int64_t *D)
 {
-    if (!g || n_theta <= 0 || n_rho <= 0 || !(g->rho_max > g->rho_min))
-        return -1;
-    double two_k = ldexp(1.0, ORACLE_FRAC_BITS);
+    double two_k = ldexp(1.0, k);
     double span = g->rho_max - g->rho_min;
     double cos_scale = two_k * (double)n_rho / (span * (double)g->phi_u_per_deg);
     double sin_scale = two_k * (double)n_rho / (span * (double)g->z_u_per_mm);
@@ -120,7 +124,29 @@ int oracle_tables(const oracle_geometry *g, int n_theta, int n_rho, int32_t *C, 
         S[t] = (int32_t)round_half_away(sin(theta) * sin_scale);
     }
     *D = round_half_away(-g->rho_min * (two_k * (double)n_rho / span));
-    return 0;
+}
+
+int oracle_tables(const oracle_geometry *g, int n_theta, int n_rho, int32_t *C, int32_t *S,
+                  int64_t *D)
+{
+    if (!g || n_theta <= 0 || n_rho <= 0 || !(g->rho_max > g->rho_min))
+        return -1;
+    int64_t phi_corner[2] = {0, (int64_t)360 * g->phi_u_per_deg - 1};
+    int64_t z_corner[2] = {g->z_min_u, (int64_t)g->z_min_u + (int64_t)g->n_z_strips * g->z_pitch_u};
+    for (int k = ORACLE_MAX_FRAC_BITS; k >= 8; --k) {
+        tables_at(g, n_theta, n_rho, k, C, S, D);
+        int fits = 1;
+        for (int t = 0; t < n_theta && fits; ++t)
+            for (int i = 0; i < 2 && fits; ++i)
+                for (int j = 0; j < 2 && fits; ++j) {
+                    int64_t v = phi_corner[i] * C[t] + z_corner[j] * S[t] + *D;
+                    if (v >= ((int64_t)1 << 31) || v < -((int64_t)1 << 31))
+                        fits = 0;
+                }
+        if (fits)
+            return k;
+    }
+    return -1;
 }
 
 /*
@@ -148,11 +174,11 @@ static int hit_is_valid(const oracle_geometry *g, int32_t phi, int32_t z)
     return phi >= 0 && (int64_t)phi < phi_end && z >= g->z_min_u && (int64_t)z <= z_end;
 }
 
-/* The rho bin of one hit in one theta row. */
-static int64_t rho_bin(int32_t phi, int32_t z, int32_t c, int32_t s, int64_t d)
+/* The rho bin of one hit in one theta row, for tables at scale 2^k. */
+static int64_t rho_bin(int32_t phi, int32_t z, int32_t c, int32_t s, int64_t d, int k)
 {
     int64_t value = (int64_t)phi * (int64_t)c + (int64_t)z * (int64_t)s + d;
-    return floor_div(value, (int64_t)1 << ORACLE_FRAC_BITS);
+    return floor_div(value, (int64_t)1 << k);
 }
 
 /*
@@ -166,13 +192,13 @@ int64_t oracle_vote(const oracle_geometry *g, int n_theta, int n_rho, const int3
     int32_t *S = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_theta);
     int64_t D = 0;
     int64_t dropped = 0;
-    oracle_tables(g, n_theta, n_rho, C, S, &D);
+    int k = oracle_tables(g, n_theta, n_rho, C, S, &D);
     memset(acc, 0, sizeof(int32_t) * (size_t)n_theta * (size_t)n_rho);
     for (int64_t h = 0; h < n_hits; ++h) {
         if (!hit_is_valid(g, phi_q[h], z_q[h]))
             continue;
         for (int t = 0; t < n_theta; ++t) {
-            int64_t b = rho_bin(phi_q[h], z_q[h], C[t], S[t], D);
+            int64_t b = rho_bin(phi_q[h], z_q[h], C[t], S[t], D, k);
             if (b >= 0 && b < n_rho)
                 acc[(size_t)t * n_rho + (size_t)b] += 1;
             else
@@ -209,10 +235,10 @@ void oracle_bins_fixed(const oracle_geometry *g, int n_theta, int n_rho, const i
     int32_t *C = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_theta);
     int32_t *S = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_theta);
     int64_t D = 0;
-    oracle_tables(g, n_theta, n_rho, C, S, &D);
+    int k = oracle_tables(g, n_theta, n_rho, C, S, &D);
     for (int64_t h = 0; h < n_hits; ++h)
         for (int t = 0; t < n_theta; ++t)
-            bins[h * n_theta + t] = rho_bin(phi_q[h], z_q[h], C[t], S[t], D);
+            bins[h * n_theta + t] = rho_bin(phi_q[h], z_q[h], C[t], S[t], D, k);
     free(C);
     free(S);
 }
@@ -346,7 +372,7 @@ int oracle_find_window(const oracle_geometry *g, int n_theta, int n_rho,
     int32_t *C = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_theta);
     int32_t *S = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_theta);
     int64_t D = 0;
-    oracle_tables(g, n_theta, n_rho, C, S, &D);
+    int k = oracle_tables(g, n_theta, n_rho, C, S, &D);
     for (int64_t h = 0; h < n_hits; ++h) {
         if (!hit_is_valid(g, phi_q[h], z_q[h])) {
             hit_track[h] = -2;
@@ -355,7 +381,7 @@ int oracle_find_window(const oracle_geometry *g, int n_theta, int n_rho,
         hit_track[h] = -1;
         for (int32_t p = 0; p < kept; ++p) {
             int t = peaks[p].theta;
-            int64_t bh = rho_bin(phi_q[h], z_q[h], C[t], S[t], D);
+            int64_t bh = rho_bin(phi_q[h], z_q[h], C[t], S[t], D, k);
             int64_t diff = bh - (int64_t)peaks[p].rho;
             if (diff < 0)
                 diff = -diff;

@@ -25,10 +25,13 @@ struct hough_ctx {
     int n_theta = 0, n_rho = 0;
     std::vector<int32_t> C, S;
     long long D = 0;
+    int K = 0;
+    bool in_range = false;   // every valid hit votes inside [0, n_rho) in every row
     int32_t *d_C = nullptr, *d_S = nullptr;
     hough_launch launch{};
     int num_sms = 0;
     size_t smem_optin = 0;
+    size_t smem_per_sm = 0;
     std::unordered_map<cudaStream_t, unsigned int *> counters;
     int last_error = HOUGH_OK;
     long long launches = 0;
@@ -75,13 +78,23 @@ int next_pow2(int x)
     return n;
 }
 
-int stride_for(int n_rho)
+// Candidate-list entries: whatever shared memory the tile leaves, up to 16
+// per 16-byte group of the tile plus one per bin of the carried row (then no
+// list can overflow).  Returns -1 when fewer than min(4096, that worst case)
+// would fit.
+int cl_entries_for(const hough_ctx *ctx, int word_rows, int hit_stage, int ctas, int threads)
 {
-    // smallest stride >= n_rho with stride = 1 (mod 32)
-    int s = n_rho;
-    while ((s & 31) != 1)
-        ++s;
-    return s;
+    const int nw = threads / 32;
+    const size_t budget = std::min(ctx->smem_optin, ctx->smem_per_sm / (size_t)ctas - 1024);
+    hk::SmemLayout L0 = hk::smem_layout(word_rows, hit_stage, ctx->n_rho, 0, nw);
+    long long room = L0.total < budget ? (long long)((budget - L0.total) / 4) : 0;
+    long long worst = 4LL * word_rows * ctx->n_rho + ctx->n_rho;
+    worst += (4 * nw) - worst % (4 * nw);
+    long long n = std::min(room, worst);
+    n -= n % (4 * nw);
+    if (n < std::min(4096LL, worst))
+        return -1;
+    return (int)n;
 }
 
 // Fill in defaults and check a launch shape against the device limits.
@@ -98,8 +111,9 @@ int resolve_launch(const hough_ctx *ctx, const hough_launch &in, hough_launch &o
         // the largest tile that fits, as long as 16-bit tiles do not pass n_theta
         l.word_rows = 32;
         for (int wr : {128, 64}) {
-            hk::SmemLayout L = hk::smem_layout(wr, stride_for(ctx->n_rho), l.hit_stage, ctx->n_rho);
-            if (L.total <= ctx->smem_optin / (size_t)l.ctas_per_sm && ctx->n_theta >= 2 * wr) {
+            hk::SmemLayout L = hk::smem_layout(wr, l.hit_stage, ctx->n_rho, 4096, l.threads / 32);
+            if ((L.total + 1024) * (size_t)l.ctas_per_sm <= ctx->smem_per_sm && L.total <= ctx->smem_optin &&
+                ctx->n_theta >= 2 * wr) {
                 l.word_rows = wr;
                 break;
             }
@@ -113,7 +127,10 @@ int resolve_launch(const hough_ctx *ctx, const hough_launch &in, hough_launch &o
         return HOUGH_ERR_INVALID_ARG;
     if (l.ctas_per_sm < 1 || l.ctas_per_sm > 4)
         return HOUGH_ERR_INVALID_ARG;
-    hk::SmemLayout L = hk::smem_layout(l.word_rows, stride_for(ctx->n_rho), l.hit_stage, ctx->n_rho);
+    const int cl = cl_entries_for(ctx, l.word_rows, l.hit_stage, l.ctas_per_sm, l.threads);
+    if (cl < 0)
+        return HOUGH_ERR_UNSUPPORTED_SHAPE;    // no room for useful candidate lists
+    hk::SmemLayout L = hk::smem_layout(l.word_rows, l.hit_stage, ctx->n_rho, cl, l.threads / 32);
     if (L.total > ctx->smem_optin)
         return HOUGH_ERR_UNSUPPORTED_SHAPE;
     out = l;
@@ -163,7 +180,9 @@ hk::KParams make_params(const hough_ctx *ctx, const hough_hits *hits, const int6
     p.n_windows = n_windows;
     p.C = ctx->d_C;
     p.S = ctx->d_S;
-    p.D = ctx->D;
+    p.D = (int)ctx->D;
+    p.K = ctx->K;
+    p.in_range = ctx->in_range ? 1 : 0;
     p.n_theta = ctx->n_theta;
     p.n_rho = ctx->n_rho;
     p.T = ctx->th.vote_threshold;
@@ -179,9 +198,13 @@ hk::KParams make_params(const hough_ctx *ctx, const hough_hits *hits, const int6
     p.acc = out->acc;
     p.work = counter;
     p.word_rows = l.word_rows;
-    p.stride = stride_for(ctx->n_rho);
+    p.lw = l.word_rows == 32 ? 5 : (l.word_rows == 64 ? 6 : 7);
+    p.nrho_inv = (unsigned)(((1ull << 32) + (unsigned long long)ctx->n_rho - 1) /
+                            (unsigned long long)ctx->n_rho);
     p.hit_stage = l.hit_stage;
     p.kp = std::max(32, next_pow2(std::max(1, ctx->th.max_peaks)));
+    p.seg_cl = cl_entries_for(ctx, l.word_rows, l.hit_stage, l.ctas_per_sm, l.threads) /
+               (l.threads / 32);
     return p;
 }
 
@@ -267,25 +290,41 @@ int check_find_args(hough_ctx *ctx, const hough_hits *hits, const int64_t *offse
 extern "C" {
 
 int hough_tables(const hough_geometry *g, int n_theta, int n_rho, int32_t *C, int32_t *S,
-                 int64_t *D)
+                 int64_t *D, int32_t *K)
 {
-    if (!geometry_ok(g) || n_theta <= 0 || n_rho <= 0 || !C || !S || !D)
+    if (!geometry_ok(g) || n_theta <= 0 || n_rho <= 0 || !C || !S || !D || !K)
         return HOUGH_ERR_INVALID_ARG;
-    const double two_k = std::ldexp(1.0, HOUGH_FRAC_BITS);
     const double span = g->rho_max - g->rho_min;
-    const double cs = two_k * (double)n_rho / (span * (double)g->phi_u_per_deg);
-    const double ss = two_k * (double)n_rho / (span * (double)g->z_u_per_mm);
     const double step = M_PI / (double)n_theta;
-    for (int t = 0; t < n_theta; ++t) {
-        double th = ((double)t + 0.5) * step;
-        double c = std::cos(th) * cs, s = std::sin(th) * ss;
-        if (!(std::fabs(c) < 2147483647.0 && std::fabs(s) < 2147483647.0))
-            return HOUGH_ERR_UNSUPPORTED_SHAPE;
-        C[t] = (int32_t)round_half_away(c);
-        S[t] = (int32_t)round_half_away(s);
+    // the four corners of the detector box (the sum is linear in phi and z)
+    const long long phis[2] = {0, 360LL * g->phi_u_per_deg - 1};
+    const long long zs[2] = {g->z_min_u, (long long)g->z_min_u + (long long)g->n_z_strips * g->z_pitch_u};
+    for (int k = HOUGH_MAX_FRAC_BITS; k >= 8; --k) {
+        const double scale = std::ldexp((double)n_rho, k) / span;
+        const double cs = scale / (double)g->phi_u_per_deg;
+        const double ss = scale / (double)g->z_u_per_mm;
+        const long long d = round_half_away(-g->rho_min * scale);
+        bool fits = d >= -(1LL << 31) && d < (1LL << 31);
+        for (int t = 0; t < n_theta && fits; ++t) {
+            const double th = ((double)t + 0.5) * step;
+            const long long c = round_half_away(std::cos(th) * cs);
+            const long long s = round_half_away(std::sin(th) * ss);
+            C[t] = (int32_t)c;
+            S[t] = (int32_t)s;
+            for (long long ph : phis)
+                for (long long z : zs) {
+                    const long long v = ph * c + z * s + d;
+                    if (v < -(1LL << 31) || v >= (1LL << 31))
+                        fits = false;
+                }
+        }
+        if (fits) {
+            *D = d;
+            *K = k;
+            return HOUGH_OK;
+        }
     }
-    *D = (int64_t)round_half_away(-g->rho_min * (two_k * (double)n_rho / span));
-    return HOUGH_OK;
+    return HOUGH_ERR_UNSUPPORTED_SHAPE;
 }
 
 int hough_create(const hough_geometry *g, int n_theta, int n_rho, const hough_thresholds *th,
@@ -318,12 +357,30 @@ int hough_create(const hough_geometry *g, int n_theta, int n_rho, const hough_th
     ctx->C.resize(n_theta);
     ctx->S.resize(n_theta);
     int64_t D = 0;
-    int rc = hough_tables(g, n_theta, n_rho, ctx->C.data(), ctx->S.data(), &D);
+    int32_t K = 0;
+    int rc = hough_tables(g, n_theta, n_rho, ctx->C.data(), ctx->S.data(), &D, &K);
     if (rc != HOUGH_OK) {
         delete ctx;
         return rc;
     }
     ctx->D = D;
+    ctx->K = K;
+    // Do all valid hits vote inside [0, n_rho) in every row?  The bin is
+    // monotone in phi and in z, so the box corners bound it.
+    {
+        const long long phis[2] = {0, 360LL * g->phi_u_per_deg - 1};
+        const long long zs[2] = {g->z_min_u, (long long)g->z_min_u + (long long)g->n_z_strips * g->z_pitch_u};
+        bool ok = true;
+        for (int t = 0; t < n_theta && ok; ++t)
+            for (long long ph : phis)
+                for (long long z : zs) {
+                    const long long v = ph * ctx->C[t] + z * ctx->S[t] + D;
+                    const long long b = v >= 0 ? (v >> K) : -((-v + (1LL << K) - 1) >> K);
+                    if (b < 0 || b >= n_rho)
+                        ok = false;
+                }
+        ctx->in_range = ok;
+    }
     int smem_optin = 0;
     if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
@@ -332,7 +389,15 @@ int hough_create(const hough_geometry *g, int n_theta, int n_rho, const hough_th
         return HOUGH_ERR_CUDA;
     }
     // the kernel's static shared scalars share the per-block limit
-    ctx->smem_optin = (size_t)smem_optin - 64;
+    ctx->smem_optin = (size_t)smem_optin - 128;
+    int smem_sm = 0;
+    if (cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
+        cudaSuccess) {
+        delete ctx;
+        return HOUGH_ERR_CUDA;
+    }
+    // each resident CTA also reserves 1 KB of shared memory for the system
+    ctx->smem_per_sm = (size_t)smem_sm;
     if (cudaMalloc(&ctx->d_C, sizeof(int32_t) * n_theta) != cudaSuccess ||
         cudaMalloc(&ctx->d_S, sizeof(int32_t) * n_theta) != cudaSuccess) {
         hough_destroy(ctx);

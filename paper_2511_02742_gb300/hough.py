@@ -17,7 +17,7 @@ import numpy as np
 from . import build as _build
 
 HOUGH_OK = 0
-HOUGH_FRAC_BITS = 24
+HOUGH_MAX_FRAC_BITS = 24
 HOUGH_MAX_THETA = 4096
 HOUGH_MAX_RHO = 1024
 HOUGH_MAX_PEAKS = 256
@@ -88,7 +88,7 @@ def load(build_if_missing: bool = False):
     lib = ctypes.CDLL(_build.LIB)
     i32, i64 = ctypes.c_int, ctypes.c_int64
     sig = {
-        "hough_tables": ([P, i32, i32, P, P, P], i32),
+        "hough_tables": ([P, i32, i32, P, P, P, P], i32),
         "hough_create": ([P, i32, i32, P, P], i32),
         "hough_destroy": ([P], None),
         "hough_encode": ([P, P, P, i64, P, P, P], i32),
@@ -151,15 +151,16 @@ def _stream(stream):
 # ----------------------------------------------------------- C-ABI functions
 
 def hough_tables(geometry: dict, n_theta: int, n_rho: int):
-    """Host-only fixed-point tables: (C int32[n_theta], S int32[n_theta], D)."""
+    """Host-only fixed-point tables: (C int32[n_theta], S int32[n_theta], D, K)."""
     lib = load()
     g = make_geometry(geometry)
     C = np.zeros(n_theta, np.int32)
     S = np.zeros(n_theta, np.int32)
     D = np.zeros(1, np.int64)
-    _check(lib.hough_tables(ctypes.byref(g), n_theta, n_rho, _ptr(C), _ptr(S), _ptr(D)),
+    K = np.zeros(1, np.int32)
+    _check(lib.hough_tables(ctypes.byref(g), n_theta, n_rho, _ptr(C), _ptr(S), _ptr(D), _ptr(K)),
            "hough_tables")
-    return C, S, int(D[0])
+    return C, S, int(D[0]), int(K[0])
 
 
 def hough_create(geometry: dict, n_theta: int, n_rho: int, vote_threshold=5, assoc_tol_bins=1,

@@ -45,17 +45,17 @@ def test_tables_equal_oracle_tables(lib):
     which are computed by independent code from the same definition."""
     from paper_2511_02742_gb300 import hough
     for n_theta, n_rho in [(180, 1000), (256, 256), (512, 512), (1024, 1024), (97, 332), (1, 4)]:
-        C, S, D = hough.hough_tables(G, n_theta, n_rho)
-        oc, os_, od = oracle.tables(G, n_theta, n_rho)
+        C, S, D, K = hough.hough_tables(G, n_theta, n_rho)
+        oc, os_, od, ok = oracle.tables(G, n_theta, n_rho)
         np.testing.assert_array_equal(C, oc)
         np.testing.assert_array_equal(S, os_)
-        assert D == od
+        assert D == od and K == ok
     geom = dict(G, rho_min=-123.5, rho_max=321.25, phi_u_per_deg=100)
-    C, S, D = hough.hough_tables(geom, 77, 444)
-    oc, os_, od = oracle.tables(geom, 77, 444)
+    C, S, D, K = hough.hough_tables(geom, 77, 444)
+    oc, os_, od, ok = oracle.tables(geom, 77, 444)
     np.testing.assert_array_equal(C, oc)
     np.testing.assert_array_equal(S, os_)
-    assert D == od
+    assert D == od and K == ok
 
 
 def test_status_strings(lib):
@@ -95,7 +95,7 @@ def test_null_pointers_are_rejected(lib):
     assert lib.hough_last_error(None) == -1
     assert lib.hough_launch_count(None) == 0
     C = np.zeros(4, np.int32)
-    assert lib.hough_tables(None, 4, 4, C.ctypes.data_as(ctypes.c_void_p), None, None) == -1
+    assert lib.hough_tables(None, 4, 4, C.ctypes.data_as(ctypes.c_void_p), None, None, None) == -1
 
 
 def test_no_device_is_reported_not_faked(lib):

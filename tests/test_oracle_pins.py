@@ -75,43 +75,81 @@ def test_encoding_phi_is_vane_angle_and_z_is_strip_centre():
 
 # ----------------------------------------------------------------- voting ---
 
+def edge_margin(geom, n_theta, n_rho):
+    """Largest possible distance, in bins, between the fixed-point bin
+    coordinate and the exact one: each table entry is within 1/2 unit of its
+    real factor, so the sum is off by at most (|phi| + |z| + 1) / 2 units of
+    2^-K bins over the detector box."""
+    k = oracle.tables(geom, n_theta, n_rho)[3]
+    phi_max = 360 * geom["phi_u_per_deg"]
+    z_max = max(abs(geom["z_min_u"]),
+                abs(geom["z_min_u"] + geom["n_z_strips"] * geom["z_pitch_u"]))
+    return 0.5 * (phi_max + z_max + 1) / 2.0 ** k + 1e-9
+
+
 @pytest.mark.parametrize("n_theta,n_rho", SHAPES)
 def test_fixed_point_bins_within_one_bin_of_fp64(n_theta, n_rho):
     """Eq. (1) + Section 5 binning: the integer bin from the fixed-point tables
     equals floor of the FP64 rho coordinate, except where that coordinate lies
-    within 0.02 bin of an edge, and is never more than one bin away."""
+    within the table-rounding margin of an edge, and is never more than one
+    bin away."""
     rng = np.random.default_rng(11)
     phi, z = random_valid_hits(rng, 400, any_phi=True)
     fixed = oracle.bins_fixed(G, n_theta, n_rho, phi, z)
     x = fp64_rho_bins(G, n_theta, n_rho, phi, z)
     ref = np.floor(x).astype(np.int64)
     assert np.abs(fixed - ref).max() <= 1
+    eps = edge_margin(G, n_theta, n_rho)
+    assert eps < 0.05
     frac = x - np.floor(x)
-    safe = (frac > 0.02) & (frac < 0.98)
-    assert safe.mean() > 0.9
+    safe = (frac > eps) & (frac < 1.0 - eps)
+    assert safe.mean() > 0.85
     np.testing.assert_array_equal(fixed[safe], ref[safe])
     # the oracle's own FP64 variant agrees with this independent computation
     fp = oracle.bins_fp64(G, n_theta, n_rho, phi, z)
-    np.testing.assert_array_equal(fp[safe], ref[safe])
+    safe64 = (frac > 1e-9) & (frac < 1.0 - 1e-9)
+    np.testing.assert_array_equal(fp[safe64], ref[safe64])
 
 
 @pytest.mark.parametrize("n_theta,n_rho", SHAPES)
 def test_tables_round_to_nearest(n_theta, n_rho):
     """The fixed-point cos/sin factors of Eq. (1) are rounded to the nearest
     integer: each entry is within half a unit of the real factor
-    cos(theta_t) * 2^24 * n_rho / (1000 deg * 200 u/deg), and likewise for sin."""
-    C, S, D = oracle.tables(G, n_theta, n_rho)
+    cos(theta_t) * 2^K * n_rho / (1000 deg * 200 u/deg), and likewise for sin."""
+    C, S, D, K = oracle.tables(G, n_theta, n_rho)
     theta = (np.arange(n_theta) + 0.5) * math.pi / n_theta
-    scale = 2.0 ** 24 * n_rho / (1000.0 * 200.0)
+    scale = 2.0 ** K * n_rho / (1000.0 * 200.0)
     assert np.abs(C - np.cos(theta) * scale).max() <= 0.5 + 1e-6
     assert np.abs(S - np.sin(theta) * scale).max() <= 0.5 + 1e-6
-    assert D == (n_rho // 2) << 24          # rho_min = -500 is exactly n_rho/2 bins below 0
+    assert D == (n_rho // 2) << K          # rho_min = -500 is exactly n_rho/2 bins below 0
+
+
+@pytest.mark.parametrize("n_theta,n_rho", SHAPES + [(64, 4), (512, 1024)])
+def test_scale_is_the_largest_that_fits_32_bits(n_theta, n_rho):
+    """The scale 2^K is the largest (K <= 24) for which every hit of the
+    detector box gives |phi*C + z*S + D| < 2^31 (checked here on a dense grid
+    of the box with exact integers), and 2^(K+1) would not fit."""
+    C, S, D, K = oracle.tables(G, n_theta, n_rho)
+    phi = np.array([0, 1800 * 20, 72000 - 1], dtype=object)
+    z = np.array([-38912, 0, 38912], dtype=object)
+    vals = [int(p_) * int(c) + int(z_) * int(s_) + D for c, s_ in zip(C, S) for p_ in phi for z_ in z]
+    assert max(abs(v) for v in vals) < 2 ** 31
+    assert 8 <= K <= 24
+    if K < 24:
+        # one more bit would overflow somewhere: double the scale by hand
+        theta = (np.arange(n_theta) + 0.5) * math.pi / n_theta
+        scale = 2.0 ** (K + 1) * n_rho / (1000.0 * 200.0)
+        C2 = np.floor(np.abs(np.cos(theta) * scale) + 0.5) * np.sign(np.cos(theta))
+        S2 = np.floor(np.abs(np.sin(theta) * scale) + 0.5)
+        D2 = (n_rho // 2) << (K + 1)
+        big = max(abs(int(p_) * int(c) + int(z_) * int(s_) + D2)
+                  for c, s_ in zip(C2, S2) for p_ in (0, 71999) for z_ in (-38912, 38912))
+        assert big >= 2 ** 31
 
 
 def test_fixed_point_edges_of_rho_range():
-    """Section 5: rho in [-500, 500) over n_rho bins; rho_min maps to bin 0 and
-    a point just below rho_max to bin n_rho - 1.  With phi = 0, z = 0, rho = 0
-    sits on the edge between bins n_rho/2 - 1 and n_rho/2 and floors up."""
+    """Section 5: rho in [-500, 500) over n_rho bins.  With phi = 0, z = 0,
+    rho = 0 sits on the edge between bins n_rho/2 - 1 and n_rho/2 and floors up."""
     for n_theta, n_rho in SHAPES:
         b = oracle.bins_fixed(G, n_theta, n_rho, np.array([0], np.int32), np.array([0], np.int32))
         assert np.all(b == n_rho // 2)
@@ -123,6 +161,7 @@ def test_accumulator_matches_fp64_brute_force(n_theta, n_rho):
     accumulator equals a brute-force FP64 histogram everywhere except in bins
     touched by a vote that lies within 0.02 bin of an edge."""
     rng = np.random.default_rng(n_theta * 1000 + n_rho)
+    eps = edge_margin(G, n_theta, n_rho)
     for trial in range(20):
         n = int(rng.integers(0, 9))
         phi, z = random_valid_hits(rng, n, any_phi=bool(trial % 2))
@@ -136,7 +175,7 @@ def test_accumulator_matches_fp64_brute_force(n_theta, n_rho):
                 if 0 <= b[h, t] < n_rho:
                     ref[t, b[h, t]] += 1
                 fr = x[h, t] - b[h, t]
-                if fr < 0.02 or fr > 0.98:
+                if fr < eps or fr > 1.0 - eps:
                     lo = max(b[h, t] - 1, -1)
                     near[t, lo + 1:b[h, t] + 3] = True
         near = near[:, 1:n_rho + 1]
@@ -158,8 +197,9 @@ def test_vote_conservation_and_row_sums():
         assert dropped > 0
         assert acc.sum() + dropped == 300 * n_theta
         x = fp64_rho_bins(geom, n_theta, n_rho, phi[:300], z[:300])
-        inside = (x >= 0.02) & (x < n_rho - 0.02)
-        maybe = (x > -0.02) & (x < n_rho + 0.02)
+        eps = edge_margin(geom, n_theta, n_rho)
+        inside = (x >= eps) & (x < n_rho - eps)
+        maybe = (x > -eps) & (x < n_rho + eps)
         rows = acc.sum(axis=1)
         assert np.all(rows >= inside.sum(axis=0))
         assert np.all(rows <= maybe.sum(axis=0))
@@ -355,7 +395,8 @@ def test_association_two_lines_first_peak_wins():
     for h in range(len(phi)):
         da = abs(math.floor(x[h, ta]) - ba)
         db = abs(math.floor(x[h, tb]) - bb)
-        if not all(0.02 < fr < 0.98 for fr in (x[h, ta] % 1.0, x[h, tb] % 1.0)):
+        eps = edge_margin(G, n_theta, n_rho)
+        if not all(eps < fr < 1.0 - eps for fr in (x[h, ta] % 1.0, x[h, tb] % 1.0)):
             continue                         # FP64 and fixed point may differ by one bin here
         checked += 1
         if da <= 1:
