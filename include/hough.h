@@ -247,6 +247,38 @@ int hough_autotune(hough_ctx *ctx, const hough_hits *hits, const int64_t *window
                    int64_t n_windows, const hough_tracks *tracks_out, void *stream, int iters,
                    hough_launch *best);
 
+/*
+ * hough_find without any allocation (no counterpart in the paper: it serves
+ * callers, not the method).  Some callers cannot call cudaMalloc -- code that
+ * runs where the device allocator is off limits (a real-time loop that must
+ * not block in the allocator, a process whose device memory is handed out by
+ * its host framework, a sandbox without allocation rights) -- and so cannot
+ * create a context.  This entry point takes the context's arguments directly
+ * and does the work of hough_find with no cudaMalloc, cudaFree or other
+ * allocating call: the small global memory the kernel needs beyond the
+ * caller's buffers (the scheduling counters and the cos/sin tables) lives in
+ * a file-scope device array of fixed size, HOUGH_NOALLOC_SCRATCH_BYTES,
+ * which every GPU that loads the library holds until the process exits.
+ *   - n_theta may be at most HOUGH_NOALLOC_MAX_THETA; larger shapes get
+ *     HOUGH_ERR_UNSUPPORTED_SHAPE.  Other arguments as hough_find (device
+ *     pointers), with the default launch shape.
+ *   - The first call on a device, with that device current, looks up the
+ *     array's device address (set-up); make that first call before any stream
+ *     capture.
+ *   - Every call on a device shares the array and leaves its contents behind:
+ *     the call clears the counters and rewrites the tables on its stream
+ *     before the kernel runs.  Calls whose work overlaps on the GPU (other
+ *     streams, other host threads) race on the array: serialise them.
+ * Errors: INVALID_ARG, UNSUPPORTED_SHAPE, NO_DEVICE, CUDA.
+ */
+#define HOUGH_NOALLOC_MAX_THETA 4096
+#define HOUGH_NOALLOC_MAX_DEVICES 64
+#define HOUGH_NOALLOC_SCRATCH_BYTES (256 + 8 * HOUGH_NOALLOC_MAX_THETA)
+int hough_find_noalloc(const hough_geometry *g, int n_theta, int n_rho,
+                       const hough_thresholds *th, const hough_hits *hits,
+                       const int64_t *window_offsets, int64_t n_windows,
+                       const hough_tracks *tracks_out, void *stream);
+
 /* Human-readable name of a hough_status value. */
 const char *hough_status_string(int status);
 

@@ -42,6 +42,40 @@ struct hough_ctx {
     cudaEvent_t host_events[2] = {nullptr, nullptr};
 };
 
+// Whether every valid hit votes inside [0, n_rho) in every row: the bin is
+// monotone in phi and in z, so the four corners of the detector box bound it.
+static bool box_votes_in_range(const hough_geometry *g, int n_theta, int n_rho, const int32_t *C,
+                               const int32_t *S, long long D, int K)
+{
+    const long long phis[2] = {0, 360LL * g->phi_u_per_deg - 1};
+    const long long zs[2] = {g->z_min_u, (long long)g->z_min_u + (long long)g->n_z_strips * g->z_pitch_u};
+    for (int t = 0; t < n_theta; ++t)
+        for (long long ph : phis)
+            for (long long z : zs) {
+                const long long v = ph * C[t] + z * S[t] + D;
+                const long long b = v >= 0 ? (v >> K) : -((-v + (1LL << K) - 1) >> K);
+                if (b < 0 || b >= n_rho)
+                    return false;
+            }
+    return true;
+}
+
+// SM count and shared-memory limits of device dev.
+static int device_limits(hough_ctx *ctx, int dev)
+{
+    int smem_optin = 0, smem_sm = 0;
+    if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
+            cudaSuccess)
+        return HOUGH_ERR_CUDA;
+    // the kernel's static shared scalars share the per-block limit
+    ctx->smem_optin = (size_t)smem_optin - 128;
+    ctx->smem_per_sm = (size_t)smem_sm;
+    return HOUGH_OK;
+}
+
 struct hough_plan {
     hough_ctx *ctx = nullptr;
     cudaGraph_t graph = nullptr;
@@ -365,39 +399,11 @@ int hough_create(const hough_geometry *g, int n_theta, int n_rho, const hough_th
     }
     ctx->D = D;
     ctx->K = K;
-    // Do all valid hits vote inside [0, n_rho) in every row?  The bin is
-    // monotone in phi and in z, so the box corners bound it.
-    {
-        const long long phis[2] = {0, 360LL * g->phi_u_per_deg - 1};
-        const long long zs[2] = {g->z_min_u, (long long)g->z_min_u + (long long)g->n_z_strips * g->z_pitch_u};
-        bool ok = true;
-        for (int t = 0; t < n_theta && ok; ++t)
-            for (long long ph : phis)
-                for (long long z : zs) {
-                    const long long v = ph * ctx->C[t] + z * ctx->S[t] + D;
-                    const long long b = v >= 0 ? (v >> K) : -((-v + (1LL << K) - 1) >> K);
-                    if (b < 0 || b >= n_rho)
-                        ok = false;
-                }
-        ctx->in_range = ok;
-    }
-    int smem_optin = 0;
-    if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
-            cudaSuccess) {
+    ctx->in_range = box_votes_in_range(g, n_theta, n_rho, ctx->C.data(), ctx->S.data(), D, K);
+    if (device_limits(ctx, dev) != HOUGH_OK) {
         delete ctx;
         return HOUGH_ERR_CUDA;
     }
-    // the kernel's static shared scalars share the per-block limit
-    ctx->smem_optin = (size_t)smem_optin - 128;
-    int smem_sm = 0;
-    if (cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
-        cudaSuccess) {
-        delete ctx;
-        return HOUGH_ERR_CUDA;
-    }
-    // each resident CTA also reserves 1 KB of shared memory for the system
-    ctx->smem_per_sm = (size_t)smem_sm;
     if (cudaMalloc(&ctx->d_C, sizeof(int32_t) * n_theta) != cudaSuccess ||
         cudaMalloc(&ctx->d_S, sizeof(int32_t) * n_theta) != cudaSuccess) {
         hough_destroy(ctx);
@@ -476,6 +482,104 @@ int hough_find(hough_ctx *ctx, const hough_hits *hits, const int64_t *window_off
         return fail(ctx, HOUGH_ERR_ALLOC);
     rc = launch_find(ctx, hits, window_offsets, n_windows, tracks_out, s, c, ctx->launch);
     return fail(ctx, rc);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- no alloc
+// hough_find_noalloc keeps the little global memory the find kernel needs
+// beyond its inputs and outputs -- the scheduling counter pair and the
+// cos/sin tables -- in this file-scope device array instead of memory from
+// cudaMalloc.  Every GPU that loads the library holds it until the process
+// exits, and every call on that GPU shares it.
+namespace {
+constexpr size_t kNoAllocCounterBytes = 256;
+constexpr size_t kNoAllocBytes =
+    kNoAllocCounterBytes + 2 * sizeof(int32_t) * (size_t)HOUGH_NOALLOC_MAX_THETA;
+std::mutex g_noalloc_mutex;
+void *g_noalloc_base[HOUGH_NOALLOC_MAX_DEVICES];   // device address of the array, per device
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+extern "C" {
+
+int hough_find_noalloc(const hough_geometry *g, int n_theta, int n_rho,
+                       const hough_thresholds *th, const hough_hits *hits,
+                       const int64_t *window_offsets, int64_t n_windows,
+                       const hough_tracks *tracks_out, void *stream)
+{
+    if (!geometry_ok(g) || !th || th->vote_threshold < 1 || th->assoc_tol_bins < 0 ||
+        th->max_peaks < 0 || !hits_ok(hits) || n_windows < 0 ||
+        n_windows >= (1ll << 31) - 65536 || (n_windows > 0 && !window_offsets))
+        return HOUGH_ERR_INVALID_ARG;
+    if (n_theta < 1 || n_theta > HOUGH_NOALLOC_MAX_THETA || n_rho < 4 || n_rho > HOUGH_MAX_RHO ||
+        n_rho % 4 != 0 || th->max_peaks > HOUGH_MAX_PEAKS)
+        return HOUGH_ERR_UNSUPPORTED_SHAPE;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return HOUGH_ERR_NO_DEVICE;
+    }
+    if (dev < 0 || dev >= HOUGH_NOALLOC_MAX_DEVICES)
+        return HOUGH_ERR_UNSUPPORTED_SHAPE;
+    // set-up, once per device, with that device current: the array's name is
+    // only a host-side stand-in, so ask the runtime for its device address
+    unsigned char *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_base[dev]) {
+            void *ptr = nullptr;
+            if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+                cudaGetLastError();
+                return HOUGH_ERR_CUDA;
+            }
+            g_noalloc_base[dev] = ptr;
+        }
+        base = static_cast<unsigned char *>(g_noalloc_base[dev]);
+    }
+    // tables on the host stack (no heap), then into the device array
+    int32_t C[HOUGH_NOALLOC_MAX_THETA], S[HOUGH_NOALLOC_MAX_THETA];
+    int64_t D = 0;
+    int32_t K = 0;
+    int rc = hough_tables(g, n_theta, n_rho, C, S, &D, &K);
+    if (rc != HOUGH_OK)
+        return rc;
+    hough_ctx ctx;          // a plain local description: nothing in it allocates or is freed
+    ctx.device = dev;
+    ctx.g = *g;
+    ctx.th = *th;
+    ctx.n_theta = n_theta;
+    ctx.n_rho = n_rho;
+    ctx.D = D;
+    ctx.K = K;
+    ctx.in_range = box_votes_in_range(g, n_theta, n_rho, C, S, D, K);
+    if (device_limits(&ctx, dev) != HOUGH_OK)
+        return HOUGH_ERR_CUDA;
+    if (!tracks_ok(&ctx, tracks_out))
+        return HOUGH_ERR_INVALID_ARG;
+    unsigned int *counter = reinterpret_cast<unsigned int *>(base);
+    ctx.d_C = reinterpret_cast<int32_t *>(base + kNoAllocCounterBytes);
+    ctx.d_S = ctx.d_C + HOUGH_NOALLOC_MAX_THETA;
+    hough_launch l{};
+    size_t smem = 0;
+    rc = resolve_launch(&ctx, hough_launch{}, l, smem);
+    if (rc != HOUGH_OK)
+        return rc;
+    ctx.launch = l;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the array keeps the last call's contents: the counters must start at 0
+    if (cudaMemsetAsync(counter, 0, 2 * sizeof(unsigned int), s) != cudaSuccess ||
+        cudaMemcpyAsync(ctx.d_C, C, sizeof(int32_t) * n_theta, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(ctx.d_S, S, sizeof(int32_t) * n_theta, cudaMemcpyHostToDevice, s) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return HOUGH_ERR_CUDA;
+    }
+    if (n_windows == 0)
+        return HOUGH_OK;
+    return launch_find(&ctx, hits, window_offsets, n_windows, tracks_out, s, counter, l);
 }
 
 int hough_find_host(hough_ctx *ctx, const hough_hits *hits, const int64_t *window_offsets,

@@ -21,6 +21,7 @@ HOUGH_MAX_FRAC_BITS = 24
 HOUGH_MAX_THETA = 4096
 HOUGH_MAX_RHO = 1024
 HOUGH_MAX_PEAKS = 256
+HOUGH_NOALLOC_MAX_THETA = 4096
 HOUGH_WIN_PEAK_OVERFLOW = 1
 HOUGH_WIN_HIT_OUT_OF_RANGE = 2
 HOUGH_WIN_VOTE_OUT_OF_RANGE = 4
@@ -100,6 +101,7 @@ def load(build_if_missing: bool = False):
         "hough_get_launch": ([P, P], i32),
         "hough_set_launch": ([P, P], i32),
         "hough_autotune": ([P, P, P, i64, P, P, i32, P], i32),
+        "hough_find_noalloc": ([P, i32, i32, P, P, P, i64, P, P], i32),
         "hough_status_string": ([i32], ctypes.c_char_p),
         "hough_last_error": ([P], i32),
         "hough_launch_count": ([P], i64),
@@ -242,6 +244,19 @@ def hough_autotune(ctx, hits: hough_hits, window_offsets, n_windows: int,
                                  ctypes.byref(tracks_out), _stream(stream), int(iters),
                                  ctypes.byref(l)), "hough_autotune")
     return l.as_dict()
+
+
+def hough_find_noalloc(geometry: dict, n_theta: int, n_rho: int, hits: hough_hits, window_offsets,
+                       n_windows: int, tracks_out: hough_tracks, vote_threshold=5,
+                       assoc_tol_bins=1, max_peaks=64, flags=0, stream=None) -> None:
+    """hough_find without a context and without any allocation (see the C
+    header): tables and counters live in the library's fixed device array."""
+    g = make_geometry(geometry)
+    th = hough_thresholds(vote_threshold, assoc_tol_bins, max_peaks, flags)
+    _check(load().hough_find_noalloc(ctypes.byref(g), n_theta, n_rho, ctypes.byref(th),
+                                     ctypes.byref(hits), _ptr(window_offsets), int(n_windows),
+                                     ctypes.byref(tracks_out), _stream(stream)),
+           "hough_find_noalloc")
 
 
 def hough_last_error(ctx) -> int:
