@@ -149,6 +149,109 @@ def _cpu_baseline(w, n_theta, n_rho, budget_s=12.0):
             "sample_single_core": f"first {n1} windows, 1 thread ({dt1:.1f} s)"}
 
 
+def _serving_leg(args, dev):
+    """Serving workload through the library's request loop (host buffers).
+
+    Windows (1-40 tracks each, 512 x 512) arrive as a Poisson process at
+    --serve-rate windows/s; every --serve-slice-ms the windows that arrived
+    form one time slice, submitted when the slice ends.  Latency = results in
+    the request's host buffers minus the slice's end.  Windows are drawn in
+    order, cyclically, from a pool generated once; every completed slice is
+    compared with the pool's one-launch results (the same windows alone)."""
+    import torch
+    from paper_2511_02742_gb300 import hough, synth
+    cfg = synth.WORKLOADS["serving"]
+    n_theta, n_rho = cfg["n_theta"], cfg["n_rho"]
+    pool = _workload("serving", args.serve_pool, 4242)
+    f = hough.Finder(n_theta, n_rho)
+    ref = f.find(dict(vane=torch.from_numpy(pool.vane).to(dev),
+                      strip=torch.from_numpy(pool.strip).to(dev)),
+                 torch.from_numpy(pool.offsets).to(dev))
+    torch.cuda.synchronize()
+    ref = {k: v.cpu().numpy() for k, v in ref.items()}
+    vane = torch.from_numpy(pool.vane).pin_memory().numpy()
+    strip = torch.from_numpy(pool.strip).pin_memory().numpy()
+    out = {k: v.numpy() for k, v in
+           f.alloc_outputs(pool.n_windows, pool.n_hits, device="cpu", pin=True).items()}
+    win_keys = ("peaks", "n_peaks", "n_found", "window_status")
+    dt_ns = int(args.serve_slice_ms * 1e6)
+    n_slices = int(round(args.serve_seconds * 1e3 / args.serve_slice_ms))
+    counts = np.random.default_rng(11).poisson(args.serve_rate * dt_ns * 1e-9, n_slices)
+    srv = hough.Server(f, n_slots=4, slot_windows=4096, slot_hits=1 << 21, max_queued=1 << 16)
+    clock = hough.hough_server_clock_ns
+    ranges, lat, bsz, bwin = {}, [], [], []
+    state = {"mism": 0, "done": 0, "last_done": 0}
+
+    def handle(rs):
+        for r in rs:
+            a, b = ranges.pop(r["ticket"])
+            lat.append((r["done_ns"] - r["arrival_ns"]) * 1e-3)
+            bsz.append(r["batch_requests"])
+            bwin.append(r["batch_windows"])
+            state["last_done"] = max(state["last_done"], r["done_ns"])
+            state["done"] += b - a
+            h0, h1 = int(pool.offsets[a]), int(pool.offsets[b])
+            ok = r["status"] == 0 and \
+                np.array_equal(out["n_peaks"][a:b], ref["n_peaks"][a:b]) and \
+                np.array_equal(out["window_status"][a:b], ref["window_status"][a:b]) and \
+                np.array_equal(out["hit_track"][h0:h1], ref["hit_track"][h0:h1]) and \
+                np.array_equal(out["track_hits"][h0:h1], ref["track_hits"][h0:h1])
+            if ok:
+                for j in range(a, b):
+                    n = int(ref["n_peaks"][j])
+                    if not np.array_equal(out["peaks"][j][:n], ref["peaks"][j][:n]):
+                        ok = False
+                        break
+            state["mism"] += 0 if ok else 1
+
+    t0 = clock() + 5_000_000
+    pos, submitted, late = 0, 0, 0
+    for i, c in enumerate(counts):
+        t_arr = t0 + (i + 1) * dt_ns
+        while True:
+            now = clock()
+            if now >= t_arr:
+                break
+            handle(srv.poll(1024))
+            if t_arr - clock() > 300_000:
+                time.sleep(1e-4)
+        if c == 0:
+            continue
+        if pos + c > pool.n_windows:
+            pos = 0
+        a, b = pos, pos + int(c)
+        pos = b
+        h0, h1 = int(pool.offsets[a]), int(pool.offsets[b])
+        o = {k: (out[k][a:b] if k in win_keys else out[k][h0:h1]) for k in out}
+        late += 1 if clock() - t_arr > 100_000 else 0
+        tk = srv.submit(vane[h0:h1], strip[h0:h1], pool.offsets[a:b + 1] - h0, o, t_arr)
+        ranges[tk] = (a, b)
+        submitted += b - a
+    srv.drain(600_000)
+    handle(srv.poll(1 << 16))
+    st = srv.stats()
+    srv.close()
+    f.close()
+    lat_a = np.array(lat)
+    span_s = (state["last_done"] - t0) * 1e-9
+    return {"workload": _workload_desc("serving", args.serve_pool) +
+            f" (pool, drawn cyclically); Poisson arrivals at {args.serve_rate:g} windows/s, "
+            f"one time slice per {args.serve_slice_ms:g} ms, {args.serve_seconds:g} s",
+            "entry_point": "hough_server_submit / hough_server_poll (pinned host buffers)",
+            "offered_windows_per_s": round(submitted / (n_slices * dt_ns * 1e-9), 1),
+            "windows_per_s": round(state["done"] / span_s, 1) if span_s > 0 else None,
+            "requests": len(lat), "windows": state["done"],
+            "p50_us": round(float(np.percentile(lat_a, 50)), 1),
+            "p99_us": round(float(np.percentile(lat_a, 99)), 1),
+            "p999_us": round(float(np.percentile(lat_a, 99.9)), 1),
+            "max_us": round(float(lat_a.max()), 1),
+            "mean_batch_requests": round(float(np.mean(bsz)), 2),
+            "mean_batch_windows": round(float(np.mean(bwin)), 1),
+            "batches": st["batches"], "late_submits": late,
+            "slots": 4, "device_bytes": st["device_bytes"],
+            "mismatched_slices": state["mism"]}
+
+
 def run_reference(args):
     rank, local_rank, world = _env_rank()
     if rank != 0:
@@ -184,6 +287,51 @@ def run_reference(args):
 
 def _flush_l2(buf):
     buf.add_(1)
+
+
+def _export_leg(args, dev, stream, flush, hbm_gbs):
+    """Accumulator-export form on the high-pileup workload (1e4 windows of ~1e3
+    hits, 1024 x 1024): the same kernel also writes every window's int32
+    accumulator (4 MiB) to HBM, so this form is bound by HBM bandwidth."""
+    import torch
+    from paper_2511_02742_gb300 import hough, synth
+    cfg = synth.WORKLOADS["high_pileup"]
+    n_theta, n_rho = cfg["n_theta"], cfg["n_rho"]
+    nw = args.export_windows
+    w = _workload("high_pileup", nw, 77)
+    f = hough.Finder(n_theta, n_rho, export_acc=True)
+    hits = dict(vane=torch.from_numpy(w.vane).to(dev), strip=torch.from_numpy(w.strip).to(dev))
+    offs = torch.from_numpy(w.offsets).to(dev)
+    out = f.alloc_outputs(w.n_windows, w.n_hits, device=dev)
+    plan = f.plan(hits, offs, out)
+    for _ in range(3):
+        hough.hough_plan_launch(plan, stream)
+    torch.cuda.synchronize()
+    steps = max(1, min(args.steps, 5))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for i in range(steps):
+        _flush_l2(flush)
+        ev[i][0].record(stream)
+        hough.hough_plan_launch(plan, stream)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    n_peaks = int(out["n_peaks"].sum().item())
+    acc_bytes = 4 * n_theta * n_rho * w.n_windows
+    algo = acc_bytes + 8 * w.n_hits + 8 * (w.n_windows + 1) + 8 * w.n_hits + 16 * n_peaks \
+        + 12 * w.n_windows
+    gbs = algo / (ms * 1e-3) / 1e9
+    hough.hough_plan_destroy(plan)
+    f.close()
+    del out, hits, offs
+    torch.cuda.empty_cache()
+    return {"workload": _workload_desc("high_pileup", nw) + ", accumulator exported",
+            "bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_gbs, "unit": "GB/s",
+            "frac": round(gbs / hbm_gbs, 4) if hbm_gbs else None,
+            "algorithmic_bytes": algo, "ms_per_step": round(ms, 3), "steps": steps,
+            "windows_per_s": round(w.n_windows / (ms * 1e-3), 2),
+            "peak_source": "measured copy bandwidth" if hbm_gbs else None}
 
 
 def run_ours(args):
@@ -320,6 +468,9 @@ def run_ours(args):
         if os.path.exists(pp):
             peaks_meas = json.load(open(pp))
         smem_peak = _smem_atomic_peak_gops(args)
+        export = _export_leg(args, dev, stream, flush, peaks_meas.get("hbm_gbs")) \
+            if args.export_windows > 0 else None
+        serving = _serving_leg(args, dev) if args.serve_seconds > 0 else None
         result = {
             "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
@@ -344,6 +495,10 @@ def run_ours(args):
                                                peaks_meas["hbm_gbs"], 4)
                                  if peaks_meas.get("hbm_gbs") else None,
                                  "algorithmic_bytes": algo_bytes}},
+            "roofline_export": export,
+            "serving": serving,
+            "latency_us": {"p50": serving["p50_us"], "p99": serving["p99_us"],
+                           "source": "serving leg"} if serving else None,
             "cpu_baseline": cpu,
             "e2e": {"value": round(w.n_windows / e2e_s, 2), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -391,6 +546,11 @@ def main():
     ap.add_argument("--windows", type=int, default=0)
     ap.add_argument("--plain-windows", type=int, default=3000)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--export-windows", type=int, default=10000)
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-rate", type=float, default=1e5)
+    ap.add_argument("--serve-slice-ms", type=float, default=1.0)
+    ap.add_argument("--serve-pool", type=int, default=20000)
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--no-probe", action="store_true")
     args = ap.parse_args()

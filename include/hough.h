@@ -49,7 +49,8 @@ typedef enum hough_status {
     HOUGH_ERR_CUDA = -3,              /* a CUDA runtime call failed               */
     HOUGH_ERR_TIMEOUT = -4,           /* a bounded device wait gave up            */
     HOUGH_ERR_UNSUPPORTED_SHAPE = -5, /* n_theta / n_rho / max_peaks out of range */
-    HOUGH_ERR_NO_DEVICE = -6          /* no usable CUDA device                    */
+    HOUGH_ERR_NO_DEVICE = -6,         /* no usable CUDA device                    */
+    HOUGH_ERR_BUSY = -7               /* a server's queue is full; retry later    */
 } hough_status;
 
 /* Per-window flags, OR-ed into tracks_out->window_status[w]. */
@@ -278,6 +279,123 @@ int hough_find_noalloc(const hough_geometry *g, int n_theta, int n_rho,
                        const hough_thresholds *th, const hough_hits *hits,
                        const int64_t *window_offsets, int64_t n_windows,
                        const hough_tracks *tracks_out, void *stream);
+
+/* ------------------------------------------------------------------ serving
+ *
+ * A request loop over one context (no counterpart in the paper, which
+ * processes the windows of a recorded sample; Section 6 makes each window an
+ * independent unit of work, which is what lets windows from different
+ * requests share a launch).  A request is one detector time slice: a CSR
+ * batch of windows in HOST memory.  A worker thread owned by the server
+ *   - admits queued requests, oldest first, into a free batch slot while the
+ *     slot's device memory has room for their windows and hits (admission by
+ *     memory: a slot holds at most slot_windows windows and slot_hits hits);
+ *   - runs each slot as one copy in, one launch of the find kernel and one
+ *     copy out, on the slot's own stream;
+ *   - copies each request's results into its host buffers and completes it.
+ * With n_slots > 1, requests that arrive while earlier batches are on the
+ * GPU go into the next free slot at once (continuous batching), so their
+ * copies and kernels overlap with the running ones.  Device buffers and
+ * pinned staging are allocated once, in hough_server_create, and stay
+ * resident.  Each window's results are the same bits as hough_find gives it
+ * alone: windows never interact.
+ *
+ * While a server exists it owns its context: make no other call on that
+ * context (hough_find, hough_set_launch, ...) until hough_server_destroy.
+ * Server calls may be made from any host thread.
+ */
+typedef struct hough_server hough_server;
+
+typedef struct hough_server_config {
+    int32_t n_slots;       /* batches in flight at once, 1..16                          */
+    int32_t raw_hits;      /* 1: requests carry (vane, strip); 0: encoded (phi_q, z_q)   */
+    int64_t slot_windows;  /* windows one batch can hold (>= 1)                         */
+    int64_t slot_hits;     /* hits one batch can hold (>= 1)                            */
+    int64_t max_queued;    /* requests waiting for a slot before submit says BUSY (>= 1) */
+} hough_server_config;
+
+/*
+ * One time slice.  in0/in1 are vane/strip (raw_hits) or phi_q/z_q, host
+ * arrays of n_hits = window_offsets[n_windows] entries; window_offsets is a
+ * host array of n_windows + 1 int64 starting at 0 and non-decreasing.  out
+ * holds HOST buffers laid out as for hough_find (peaks[n_windows*max_peaks],
+ * n_peaks, n_found (may be NULL), hit_track[n_hits], track_hits[n_hits],
+ * window_status; acc is not supported).  Every buffer must stay valid and
+ * untouched until the request completes.  arrival_ns: when the slice arrived,
+ * on the hough_server_clock_ns clock (0 = at submit); latencies are measured
+ * from it.
+ */
+typedef struct hough_request {
+    const int32_t *in0;
+    const int32_t *in1;
+    const int64_t *window_offsets;
+    int64_t n_windows;
+    hough_tracks out;
+    int64_t arrival_ns;
+} hough_request;
+
+typedef struct hough_request_result {
+    uint64_t ticket;
+    int32_t status;          /* HOUGH_OK, or the error that ended the request    */
+    int32_t batch_requests;  /* requests that shared its launch                  */
+    int64_t batch_windows;   /* windows in that launch                           */
+    int64_t arrival_ns;      /* as submitted (or the submit time)                */
+    int64_t launch_ns;       /* when its batch was handed to the GPU             */
+    int64_t done_ns;         /* when its results were in its host buffers        */
+} hough_request_result;
+
+typedef struct hough_server_stats {
+    int64_t submitted;       /* accepted requests                                */
+    int64_t rejected;        /* submits answered BUSY or refused as too large    */
+    int64_t completed;
+    int64_t queued;          /* accepted, waiting for a slot                      */
+    int64_t in_flight;       /* requests in batches on the GPU                   */
+    int64_t batches;         /* launches so far                                  */
+    int64_t windows;         /* windows completed                                */
+    int64_t device_bytes;    /* device memory held by the slots                  */
+    int64_t host_bytes;      /* pinned host staging held by the slots            */
+} hough_server_stats;
+
+/*
+ * Create a server over ctx (current device = ctx's device).  Allocates every
+ * slot's stream, device buffers and pinned staging, and starts the worker
+ * thread.  Errors: INVALID_ARG (bad config, or ctx exports accumulators),
+ * ALLOC, CUDA.
+ */
+int hough_server_create(hough_ctx *ctx, const hough_server_config *cfg, hough_server **out);
+
+/*
+ * Queue a request; *ticket identifies it.  Checks the request on the host
+ * (pointers, offsets) and its size against one slot.  Never blocks on the
+ * GPU.  Errors: INVALID_ARG, UNSUPPORTED_SHAPE (more windows or hits than a
+ * slot holds), BUSY (max_queued requests already waiting).
+ */
+int hough_server_submit(hough_server *srv, const hough_request *req, uint64_t *ticket);
+
+/*
+ * Wait up to timeout_ms (< 0: no limit) for one ticket and take its result
+ * (each result is delivered once, by wait or by poll).  Errors: INVALID_ARG
+ * (unknown or already delivered ticket), TIMEOUT.
+ */
+int hough_server_wait(hough_server *srv, uint64_t ticket, int64_t timeout_ms,
+                      hough_request_result *res);
+
+/* Take up to cap completed results, oldest completion first; *n receives
+ * how many were written.  Never blocks. */
+int hough_server_poll(hough_server *srv, hough_request_result *res, int64_t cap, int64_t *n);
+
+/* Wait up to timeout_ms (< 0: no limit) until nothing is queued or in
+ * flight.  Errors: TIMEOUT. */
+int hough_server_drain(hough_server *srv, int64_t timeout_ms);
+
+int hough_server_get_stats(hough_server *srv, hough_server_stats *out);
+
+/* Finish every accepted request, stop the worker and free the slots.  NULL
+ * is a no-op.  The context stays valid. */
+void hough_server_destroy(hough_server *srv);
+
+/* The server's clock (monotonic, nanoseconds), for arrival_ns. */
+int64_t hough_server_clock_ns(void);
 
 /* Human-readable name of a hough_status value. */
 const char *hough_status_string(int status);

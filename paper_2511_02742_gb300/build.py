@@ -1,7 +1,9 @@
 """Build libhough.so (the CUDA path) in-tree with nvcc for sm_103a.
 
-The library is one translation unit (host C ABI + kernels), linked against the
-static CUDA runtime so that the shared object only needs the driver.
+The library is two translation units -- the C ABI with the kernels
+(hough_api.cu) and the host-only request loop (hough_server.cpp) -- linked
+against the static CUDA runtime so that the shared object only needs the
+driver.
 """
 from __future__ import annotations
 
@@ -13,7 +15,9 @@ import sys
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 SRC = os.path.join(PKG, "csrc", "hough_api.cu")
-DEPS = [SRC, os.path.join(PKG, "csrc", "hough_kernels.cuh"), os.path.join(ROOT, "include", "hough.h")]
+SERVER_SRC = os.path.join(PKG, "csrc", "hough_server.cpp")
+DEPS = [SRC, SERVER_SRC, os.path.join(PKG, "csrc", "hough_kernels.cuh"),
+        os.path.join(PKG, "csrc", "hough_internal.h"), os.path.join(ROOT, "include", "hough.h")]
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libhough.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
@@ -38,8 +42,8 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-           "-I", os.path.join(ROOT, "include"), "-o", tmp, SRC, *extra]
+    cmd = [nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-pthread",
+           "-shared", "-I", os.path.join(ROOT, "include"), "-o", tmp, SRC, SERVER_SRC, *extra]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     res = subprocess.run(cmd, capture_output=True, text=True)

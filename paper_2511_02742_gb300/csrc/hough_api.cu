@@ -16,31 +16,8 @@
 #include <vector>
 
 #include "hough.h"
+#include "hough_internal.h"
 #include "hough_kernels.cuh"
-
-struct hough_ctx {
-    int device = 0;
-    hough_geometry g{};
-    hough_thresholds th{};
-    int n_theta = 0, n_rho = 0;
-    std::vector<int32_t> C, S;
-    long long D = 0;
-    int K = 0;
-    bool in_range = false;   // every valid hit votes inside [0, n_rho) in every row
-    int32_t *d_C = nullptr, *d_S = nullptr;
-    hough_launch launch{};
-    int num_sms = 0;
-    size_t smem_optin = 0;
-    size_t smem_per_sm = 0;
-    std::unordered_map<cudaStream_t, unsigned int *> counters;
-    int last_error = HOUGH_OK;
-    long long launches = 0;
-    // hough_find_host staging (device), grown on demand
-    void *stage_dev = nullptr;
-    size_t stage_bytes = 0;
-    cudaStream_t host_streams[2] = {nullptr, nullptr};
-    cudaEvent_t host_events[2] = {nullptr, nullptr};
-};
 
 // Whether every valid hit votes inside [0, n_rho) in every row: the bin is
 // monotone in phi and in z, so the four corners of the detector box bound it.
@@ -114,8 +91,8 @@ int next_pow2(int x)
 
 // Candidate-list entries: whatever shared memory the tile leaves, up to 16
 // per 16-byte group of the tile plus one per bin of the carried row (then no
-// list can overflow).  Returns -1 when fewer than min(4096, that worst case)
-// would fit.
+// list can overflow).  Returns -1 when fewer than min(1024, that worst case)
+// would fit (a list that overflows only sends its tile to the direct test).
 int cl_entries_for(const hough_ctx *ctx, int word_rows, int hit_stage, int ctas, int threads)
 {
     const int nw = threads / 32;
@@ -126,7 +103,7 @@ int cl_entries_for(const hough_ctx *ctx, int word_rows, int hit_stage, int ctas,
     worst += (4 * nw) - worst % (4 * nw);
     long long n = std::min(room, worst);
     n -= n % (4 * nw);
-    if (n < std::min(4096LL, worst))
+    if (n < std::min(1024LL, worst))
         return -1;
     return (int)n;
 }
@@ -620,14 +597,30 @@ int hough_find_host(hough_ctx *ctx, const hough_hits *hits, const int64_t *windo
     }
     char *base = (char *)ctx->stage_dev;
     cudaStream_t s = (cudaStream_t)stream;
-    auto cp = [&](void *dst, const void *src, size_t n, cudaMemcpyKind k) {
-        return n == 0 || cudaMemcpyAsync(dst, src, n, k, s) == cudaSuccess;
+    auto cp = [](void *dst, const void *src, size_t n, cudaMemcpyKind k, cudaStream_t cs) {
+        return n == 0 || cudaMemcpyAsync(dst, src, n, k, cs) == cudaSuccess;
     };
-    bool ok = cp(base + o_off, window_offsets, 8 * (size_t)(n_windows + 1), cudaMemcpyHostToDevice) &&
-              cp(base + o_in0, raw ? hits->vane : hits->phi_q, 4 * (size_t)H, cudaMemcpyHostToDevice) &&
-              cp(base + o_in1, raw ? hits->strip : hits->z_q, 4 * (size_t)H, cudaMemcpyHostToDevice);
-    if (!ok)
+    // two internal streams alternate over chunks of windows, so that the
+    // copies of one chunk overlap the kernel of another; they start after
+    // the work already queued on `stream`
+    for (int i = 0; i < 2; ++i) {
+        if (!ctx->host_streams[i] &&
+            cudaStreamCreateWithFlags(&ctx->host_streams[i], cudaStreamNonBlocking) != cudaSuccess)
+            return fail(ctx, HOUGH_ERR_CUDA);
+        if (!ctx->host_events[i] &&
+            cudaEventCreateWithFlags(&ctx->host_events[i], cudaEventDisableTiming) != cudaSuccess)
+            return fail(ctx, HOUGH_ERR_CUDA);
+    }
+    if (cudaEventRecord(ctx->host_events[0], s) != cudaSuccess)
         return fail(ctx, HOUGH_ERR_CUDA);
+    unsigned int *ctr[2];
+    for (int i = 0; i < 2; ++i) {
+        ctr[i] = counter_for(ctx, ctx->host_streams[i]);
+        if (!ctr[i])
+            return fail(ctx, HOUGH_ERR_ALLOC);
+        if (cudaStreamWaitEvent(ctx->host_streams[i], ctx->host_events[0], 0) != cudaSuccess)
+            return fail(ctx, HOUGH_ERR_CUDA);
+    }
     hough_hits dh{};
     dh.n_hits = H;
     if (raw) {
@@ -645,22 +638,72 @@ int hough_find_host(hough_ctx *ctx, const hough_hits *hits, const int64_t *windo
     dt.track_hits = (int32_t *)(base + o_th);
     dt.window_status = (uint32_t *)(base + o_st);
     dt.acc = exp_acc ? (int32_t *)(base + o_acc) : nullptr;
-    unsigned int *c = counter_for(ctx, s);
-    if (!c)
-        return fail(ctx, HOUGH_ERR_ALLOC);
-    rc = launch_find(ctx, &dh, (const int64_t *)(base + o_off), n_windows, &dt, s, c, ctx->launch);
+    const int32_t *in0 = raw ? hits->vane : hits->phi_q;
+    const int32_t *in1 = raw ? hits->strip : hits->z_q;
+    // chunk k: windows [w0, w1) read hits [offsets[w0], offsets[w1]) of the
+    // whole staged arrays (offsets stay absolute), outputs land at their
+    // final places; a window whose offsets are bad reads nothing
+    const int64_t n_chunks = n_windows >= 8192 ? 4 : 1;
+    Prepared pr{};
+    rc = prepare_find(ctx, (n_windows + n_chunks - 1) / n_chunks, ctx->launch, pr);
     if (rc != HOUGH_OK)
         return fail(ctx, rc);
-    ok = cp(out->peaks, dt.peaks, sizeof(hough_peak) * (size_t)n_windows * mp, cudaMemcpyDeviceToHost) &&
-         cp(out->n_peaks, dt.n_peaks, 4 * (size_t)n_windows, cudaMemcpyDeviceToHost) &&
-         (!out->n_found || cp(out->n_found, dt.n_found, 4 * (size_t)n_windows, cudaMemcpyDeviceToHost)) &&
-         cp(out->hit_track, dt.hit_track, 4 * (size_t)H, cudaMemcpyDeviceToHost) &&
-         cp(out->track_hits, dt.track_hits, 4 * (size_t)H, cudaMemcpyDeviceToHost) &&
-         cp(out->window_status, dt.window_status, 4 * (size_t)n_windows, cudaMemcpyDeviceToHost) &&
-         (!exp_acc || cp(out->acc, dt.acc, acc_per_w * (size_t)n_windows, cudaMemcpyDeviceToHost));
-    if (!ok)
+    auto clampH = [&](int64_t v) { return std::min<int64_t>(std::max<int64_t>(v, 0), H); };
+    bool ok = true;
+    for (int64_t k = 0; k < n_chunks && ok; ++k) {
+        const int64_t w0 = n_windows * k / n_chunks, w1 = n_windows * (k + 1) / n_chunks;
+        const int64_t nw = w1 - w0;
+        // hit range of the chunk (a hull of its windows' ranges, clamped)
+        int64_t h0 = H, h1 = 0;
+        for (int64_t w = w0; w <= w1; ++w) {
+            h0 = std::min(h0, clampH(window_offsets[w]));
+            h1 = std::max(h1, clampH(window_offsets[w]));
+        }
+        if (h1 < h0)
+            h1 = h0;
+        cudaStream_t cs = ctx->host_streams[k & 1];
+        ok = cp(base + o_off + 8 * w0, window_offsets + w0, 8 * (size_t)(nw + 1),
+                cudaMemcpyHostToDevice, cs) &&
+             cp(base + o_in0 + 4 * h0, in0 + h0, 4 * (size_t)(h1 - h0), cudaMemcpyHostToDevice, cs) &&
+             cp(base + o_in1 + 4 * h0, in1 + h0, 4 * (size_t)(h1 - h0), cudaMemcpyHostToDevice, cs);
+        if (!ok)
+            break;
+        hough_tracks ct = dt;
+        ct.peaks = dt.peaks + (size_t)w0 * mp;
+        ct.n_peaks = dt.n_peaks + w0;
+        ct.n_found = dt.n_found + w0;
+        ct.window_status = dt.window_status + w0;
+        if (exp_acc)
+            ct.acc = dt.acc + (size_t)w0 * ctx->n_theta * ctx->n_rho;
+        Prepared pk = pr;
+        pk.grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(pr.grid, nw));
+        rc = enqueue_find(ctx, &dh, (const int64_t *)(base + o_off) + w0, nw, &ct, cs, ctr[k & 1], pk);
+        if (rc != HOUGH_OK)
+            return fail(ctx, rc);
+        ok = cp(out->peaks + (size_t)w0 * mp, ct.peaks, sizeof(hough_peak) * (size_t)nw * mp,
+                cudaMemcpyDeviceToHost, cs) &&
+             cp(out->n_peaks + w0, ct.n_peaks, 4 * (size_t)nw, cudaMemcpyDeviceToHost, cs) &&
+             (!out->n_found ||
+              cp(out->n_found + w0, ct.n_found, 4 * (size_t)nw, cudaMemcpyDeviceToHost, cs)) &&
+             cp(out->hit_track + h0, dt.hit_track + h0, 4 * (size_t)(h1 - h0), cudaMemcpyDeviceToHost, cs) &&
+             cp(out->track_hits + h0, dt.track_hits + h0, 4 * (size_t)(h1 - h0), cudaMemcpyDeviceToHost, cs) &&
+             cp(out->window_status + w0, ct.window_status, 4 * (size_t)nw, cudaMemcpyDeviceToHost, cs) &&
+             (!exp_acc || cp(out->acc + (size_t)w0 * ctx->n_theta * ctx->n_rho, ct.acc,
+                             acc_per_w * (size_t)nw, cudaMemcpyDeviceToHost, cs));
+    }
+    // both internal streams finish before the call returns; `stream` then
+    // waits on them too, so later work on it sees the results
+    for (int i = 0; i < 2; ++i)
+        if (cudaEventRecord(ctx->host_events[i], ctx->host_streams[i]) != cudaSuccess ||
+            cudaStreamWaitEvent(s, ctx->host_events[i], 0) != cudaSuccess)
+            ok = false;
+    if (!ok) {
+        cudaStreamSynchronize(ctx->host_streams[0]);
+        cudaStreamSynchronize(ctx->host_streams[1]);
         return fail(ctx, HOUGH_ERR_CUDA);
-    if (cudaStreamSynchronize(s) != cudaSuccess)
+    }
+    if (cudaStreamSynchronize(ctx->host_streams[0]) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->host_streams[1]) != cudaSuccess)
         return fail(ctx, HOUGH_ERR_CUDA);
     return HOUGH_OK;
 }

@@ -1,0 +1,35 @@
+// hough_internal.h -- the library's private view of a context, shared by
+// the translation units of libhough (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <unordered_map>
+#include <vector>
+
+#include "hough.h"
+
+struct hough_ctx {
+    int device = 0;
+    hough_geometry g{};
+    hough_thresholds th{};
+    int n_theta = 0, n_rho = 0;
+    std::vector<int32_t> C, S;
+    long long D = 0;
+    int K = 0;
+    bool in_range = false;   // every valid hit votes inside [0, n_rho) in every row
+    int32_t *d_C = nullptr, *d_S = nullptr;
+    hough_launch launch{};
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    size_t smem_per_sm = 0;
+    std::unordered_map<cudaStream_t, unsigned int *> counters;
+    int last_error = HOUGH_OK;
+    std::atomic<long long> launches{0};
+    // hough_find_host staging (device), grown on demand
+    void *stage_dev = nullptr;
+    size_t stage_bytes = 0;
+    cudaStream_t host_streams[2] = {nullptr, nullptr};
+    cudaEvent_t host_events[2] = {nullptr, nullptr};
+};

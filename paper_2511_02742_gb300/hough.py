@@ -27,6 +27,9 @@ HOUGH_WIN_HIT_OUT_OF_RANGE = 2
 HOUGH_WIN_VOTE_OUT_OF_RANGE = 4
 HOUGH_WIN_BAD_OFFSETS = 8
 HOUGH_FLAG_EXPORT_ACC = 1
+HOUGH_ERR_TIMEOUT = -4
+HOUGH_ERR_UNSUPPORTED_SHAPE = -5
+HOUGH_ERR_BUSY = -7
 
 PEAK_DTYPE = np.dtype([("theta", "<u2"), ("rho", "<u2"), ("votes", "<i4"),
                        ("n_hits", "<i4"), ("hit_begin", "<i4")])
@@ -58,6 +61,36 @@ class hough_tracks(ctypes.Structure):
 class hough_launch(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("word_rows", ctypes.c_int32),
                 ("hit_stage", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class hough_server_config(ctypes.Structure):
+    _fields_ = [("n_slots", ctypes.c_int32), ("raw_hits", ctypes.c_int32),
+                ("slot_windows", ctypes.c_int64), ("slot_hits", ctypes.c_int64),
+                ("max_queued", ctypes.c_int64)]
+
+
+class hough_request(ctypes.Structure):
+    _fields_ = [("in0", P), ("in1", P), ("window_offsets", P), ("n_windows", ctypes.c_int64),
+                ("out", hough_tracks), ("arrival_ns", ctypes.c_int64)]
+
+
+class hough_request_result(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32),
+                ("batch_requests", ctypes.c_int32), ("batch_windows", ctypes.c_int64),
+                ("arrival_ns", ctypes.c_int64), ("launch_ns", ctypes.c_int64),
+                ("done_ns", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class hough_server_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "rejected", "completed", "queued",
+                                               "in_flight", "batches", "windows",
+                                               "device_bytes", "host_bytes")]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -105,6 +138,14 @@ def load(build_if_missing: bool = False):
         "hough_status_string": ([i32], ctypes.c_char_p),
         "hough_last_error": ([P], i32),
         "hough_launch_count": ([P], i64),
+        "hough_server_create": ([P, P, P], i32),
+        "hough_server_submit": ([P, P, P], i32),
+        "hough_server_wait": ([P, ctypes.c_uint64, i64, P], i32),
+        "hough_server_poll": ([P, P, i64, P], i32),
+        "hough_server_drain": ([P, i64], i32),
+        "hough_server_get_stats": ([P, P], i32),
+        "hough_server_destroy": ([P], None),
+        "hough_server_clock_ns": ([], i64),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -352,3 +393,82 @@ class Finder:
         n_windows = int(offsets.numel()) - 1
         return hough_autotune(self.ctx, self.hits_struct(hits), offsets, n_windows,
                               make_tracks(out), iters, stream)
+
+
+# ------------------------------------------------------------------ serving
+
+def hough_server_clock_ns() -> int:
+    return int(load().hough_server_clock_ns())
+
+
+class Server:
+    """The request loop of libhough over one Finder's context (host buffers).
+
+    submit() queues one time slice (numpy arrays in host memory, ideally
+    pinned) and returns a ticket; the arrays are held here until the request
+    is delivered by wait() or poll().  While the server exists it owns the
+    Finder's context.
+    """
+
+    def __init__(self, finder: "Finder", n_slots=4, slot_windows=4096, slot_hits=1 << 20,
+                 max_queued=4096, raw_hits=True):
+        self.lib = load()
+        self.finder = finder
+        self.max_peaks = finder.max_peaks
+        cfg = hough_server_config(n_slots, 1 if raw_hits else 0, slot_windows, slot_hits,
+                                  max_queued)
+        h = ctypes.c_void_p()
+        _check(self.lib.hough_server_create(finder.ctx, ctypes.byref(cfg), ctypes.byref(h)),
+               "hough_server_create")
+        self.h = h
+        self.raw_hits = raw_hits
+        self._held = {}
+
+    def submit(self, in0, in1, offsets, out: dict, arrival_ns: int = 0) -> int:
+        """Queue windows (in0/in1: vane/strip or phi_q/z_q, int32; offsets int64
+        starting at 0); results go to the host arrays of `out` (as Finder
+        outputs).  Raises HoughError (code HOUGH_ERR_BUSY when the queue is full)."""
+        offsets = np.ascontiguousarray(offsets, np.int64)
+        req = hough_request(_ptr(in0), _ptr(in1), _ptr(offsets), len(offsets) - 1,
+                            make_tracks(out), int(arrival_ns))
+        t = ctypes.c_uint64()
+        _check(self.lib.hough_server_submit(self.h, ctypes.byref(req), ctypes.byref(t)),
+               "hough_server_submit")
+        self._held[int(t.value)] = (in0, in1, offsets, out)
+        return int(t.value)
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> dict:
+        r = hough_request_result()
+        _check(self.lib.hough_server_wait(self.h, ticket, timeout_ms, ctypes.byref(r)),
+               "hough_server_wait")
+        self._held.pop(ticket, None)
+        return r.as_dict()
+
+    def poll(self, cap: int = 4096) -> list:
+        buf = (hough_request_result * cap)()
+        n = ctypes.c_int64()
+        _check(self.lib.hough_server_poll(self.h, buf, cap, ctypes.byref(n)), "hough_server_poll")
+        out = [buf[i].as_dict() for i in range(n.value)]
+        for r in out:
+            self._held.pop(r["ticket"], None)
+        return out
+
+    def drain(self, timeout_ms: int = -1) -> None:
+        _check(self.lib.hough_server_drain(self.h, timeout_ms), "hough_server_drain")
+
+    def stats(self) -> dict:
+        st = hough_server_stats()
+        _check(self.lib.hough_server_get_stats(self.h, ctypes.byref(st)), "hough_server_get_stats")
+        return st.as_dict()
+
+    def close(self) -> None:
+        if self.h:
+            self.lib.hough_server_destroy(self.h)
+            self.h = None
+            self._held.clear()
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass

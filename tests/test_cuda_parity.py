@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 from paper_2511_02742_gb300 import synth
-from parity_helpers import G, assert_batch_equal, assert_window_equal, gpu_run, oracle_run
+from parity_helpers import G, assert_batch_equal, assert_window_equal, gpu_run, oracle_run, to_numpy
 
 pytestmark = pytest.mark.gpu
 
@@ -259,6 +259,29 @@ def test_plan_graph_and_host_entry_point(hough):
     c = to_numpy(oh, w.n_hits)
     for k in a:
         np.testing.assert_array_equal(a[k], c[k], err_msg=k)
+    f.close()
+
+
+def test_host_entry_point_in_chunks_with_export(hough):
+    """hough_find_host over 9000 windows (copies and kernels pipelined in
+    chunks over two streams), empty windows included, accumulators exported:
+    the same bits as the device entry point."""
+    import torch
+    w = synth.generate(9000, ("poisson", 4, 0, 12), (100.0, 300.0), 0.02, seed=21)
+    f = _finder(hough, 64, 128, export_acc=True)
+    a = gpu_run(f, w)
+    hh = dict(vane=torch.from_numpy(w.vane).pin_memory(), strip=torch.from_numpy(w.strip).pin_memory())
+    oh = f.alloc_outputs(w.n_windows, w.n_hits, device="cpu", pin=True)
+    for v in oh.values():
+        v.fill_(-3)
+    f.find_host(hh, torch.from_numpy(w.offsets), out=oh)
+    c = to_numpy(oh, w.n_hits)
+    assert (np.diff(w.offsets) == 0).any()
+    for k in ("n_peaks", "n_found", "hit_track", "track_hits", "status", "acc"):
+        np.testing.assert_array_equal(a[k], c[k], err_msg=k)
+    for k in range(w.n_windows):
+        n = int(a["n_peaks"][k])
+        np.testing.assert_array_equal(a["peaks"][k][:n], c["peaks"][k][:n])
     f.close()
 
 

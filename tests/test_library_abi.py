@@ -107,3 +107,34 @@ def test_no_device_is_reported_not_faked(lib):
     with pytest.raises(hough.HoughError) as e:
         hough.hough_create(G, 64, 64)
     assert e.value.code == -6
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every ctypes struct of the binding has the size and field offsets the C
+    compiler gives the struct of include/hough.h."""
+    import subprocess
+    from paper_2511_02742_gb300 import hough
+    structs = [hough.hough_geometry, hough.hough_thresholds, hough.hough_hits, hough.hough_tracks,
+               hough.hough_launch, hough.hough_server_config, hough.hough_request,
+               hough.hough_request_result, hough.hough_server_stats]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hough.h"', 'int main(void) {']
+    for st in structs:
+        n = st.__name__
+        lines.append(f'printf("{n} size %zu\\n", sizeof({n}));')
+        for field, _ in st._fields_:
+            lines.append(f'printf("{n} {field} %zu\\n", offsetof({n}, {field}));')
+    lines.append('printf("hough_peak size %zu\\n", sizeof(hough_peak));')
+    lines += ['return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)],
+                   check=True)
+    got = dict(line.rsplit(" ", 1) for line in
+               subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines())
+    for st in structs:
+        n = st.__name__
+        assert int(got[f"{n} size"]) == ctypes.sizeof(st), n
+        for field, _ in st._fields_:
+            assert int(got[f"{n} {field}"]) == getattr(st, field).offset, (n, field)
+    assert int(got["hough_peak size"]) == hough.PEAK_DTYPE.itemsize == 16
