@@ -303,6 +303,13 @@ def _export_leg(args, dev, stream, flush, hbm_gbs):
     hits = dict(vane=torch.from_numpy(w.vane).to(dev), strip=torch.from_numpy(w.strip).to(dev))
     offs = torch.from_numpy(w.offsets).to(dev)
     out = f.alloc_outputs(w.n_windows, w.n_hits, device=dev)
+    launch = hough.hough_get_launch(f.ctx)
+    if args.autotune:
+        sub = w.subset(np.arange(min(w.n_windows, 1000)))
+        sh = dict(vane=torch.from_numpy(sub.vane).to(dev), strip=torch.from_numpy(sub.strip).to(dev))
+        so = torch.from_numpy(sub.offsets).to(dev)
+        launch = f.autotune(sh, so, f.alloc_outputs(sub.n_windows, sub.n_hits, device=dev), iters=1)
+        launch["autotuned_on"] = f"first {sub.n_windows} windows"
     plan = f.plan(hits, offs, out)
     for _ in range(3):
         hough.hough_plan_launch(plan, stream)
@@ -330,6 +337,7 @@ def _export_leg(args, dev, stream, flush, hbm_gbs):
             "bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_gbs, "unit": "GB/s",
             "frac": round(gbs / hbm_gbs, 4) if hbm_gbs else None,
             "algorithmic_bytes": algo, "ms_per_step": round(ms, 3), "steps": steps,
+            "launch": launch,
             "windows_per_s": round(w.n_windows / (ms * 1e-3), 2),
             "peak_source": "measured copy bandwidth" if hbm_gbs else None}
 
@@ -366,6 +374,7 @@ def run_ours(args):
         so = torch.from_numpy(sub.offsets).to(dev)
         souts = f.alloc_outputs(sub.n_windows, sub.n_hits, device=dev)
         launch = f.autotune(sh, so, souts, iters=2)
+        launch["autotuned_on"] = f"first {sub.n_windows} windows"
         del sh, so, souts
     plan = f.plan(hits, offs, out)
     flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)   # 512 MB > L2
@@ -551,7 +560,8 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=1e5)
     ap.add_argument("--serve-slice-ms", type=float, default=1.0)
     ap.add_argument("--serve-pool", type=int, default=20000)
-    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the library's default launch shape instead of autotuning it")
     ap.add_argument("--no-probe", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -89,21 +89,25 @@ int next_pow2(int x)
     return n;
 }
 
-// Candidate-list entries: whatever shared memory the tile leaves, up to 16
-// per 16-byte group of the tile plus one per bin of the carried row (then no
-// list can overflow).  Returns -1 when fewer than min(1024, that worst case)
-// would fit (a list that overflows only sends its tile to the direct test).
+// Candidate-list entries: whatever shared memory the tile leaves, up to what
+// lists holding every counter of the tile and of the carried row need.
+// Returns -1 when fewer than max(1024, threads + 64 per warp) would fit: a
+// list that overflows only sends its tile to the direct test, but every
+// warp needs at least two column slots per lane and the check needs one
+// gathered entry per thread.
 int cl_entries_for(const hough_ctx *ctx, int word_rows, int hit_stage, int ctas, int threads)
 {
     const int nw = threads / 32;
     const size_t budget = std::min(ctx->smem_optin, ctx->smem_per_sm / (size_t)ctas - 1024);
     hk::SmemLayout L0 = hk::smem_layout(word_rows, hit_stage, ctx->n_rho, 0, nw);
     long long room = L0.total < budget ? (long long)((budget - L0.total) / 4) : 0;
-    long long worst = 4LL * word_rows * ctx->n_rho + ctx->n_rho;
-    worst += (4 * nw) - worst % (4 * nw);
-    long long n = std::min(room, worst);
+    // lists able to hold every counter of the tile and of the carried row in
+    // their columns, plus the gathered-entry sixth
+    const long long need = std::max<long long>(1024, threads + 64LL * nw);
+    const long long worst = (4LL * word_rows * ctx->n_rho + ctx->n_rho) * 12 / 5 + threads;
+    long long n = std::min(room, std::max(worst, need));
     n -= n % (4 * nw);
-    if (n < std::min(1024LL, worst))
+    if (n < need)
         return -1;
     return (int)n;
 }
@@ -112,6 +116,14 @@ int cl_entries_for(const hough_ctx *ctx, int word_rows, int hit_stage, int ctas,
 int resolve_launch(const hough_ctx *ctx, const hough_launch &in, hough_launch &out, size_t &smem)
 {
     hough_launch l = in;
+    // Fully default: two CTAs of 512 threads per SM with 32-word-row tiles
+    // when they fit (one CTA's barriers then overlap the other's votes),
+    // else one CTA with the largest tile.
+    if (l.threads == 0 && l.word_rows == 0 && l.hit_stage == 0 && l.ctas_per_sm == 0) {
+        const hough_launch two{512, 32, 1024, 2};
+        if (resolve_launch(ctx, two, out, smem) == HOUGH_OK)
+            return HOUGH_OK;
+    }
     if (l.threads == 0)
         l.threads = 512;
     if (l.hit_stage == 0)
@@ -141,6 +153,11 @@ int resolve_launch(const hough_ctx *ctx, const hough_launch &in, hough_launch &o
     const int cl = cl_entries_for(ctx, l.word_rows, l.hit_stage, l.ctas_per_sm, l.threads);
     if (cl < 0)
         return HOUGH_ERR_UNSUPPORTED_SHAPE;    // no room for useful candidate lists
+    // association keeps one count per warp and category in the tile or in
+    // the list area
+    const long long cat_counts = (long long)(l.threads / 32) * (ctx->th.max_peaks + 2);
+    if (cat_counts > (long long)l.word_rows * ctx->n_rho && cat_counts > cl)
+        return HOUGH_ERR_UNSUPPORTED_SHAPE;
     hk::SmemLayout L = hk::smem_layout(l.word_rows, l.hit_stage, ctx->n_rho, cl, l.threads / 32);
     if (L.total > ctx->smem_optin)
         return HOUGH_ERR_UNSUPPORTED_SHAPE;
@@ -214,8 +231,16 @@ hk::KParams make_params(const hough_ctx *ctx, const hough_hits *hits, const int6
                             (unsigned long long)ctx->n_rho);
     p.hit_stage = l.hit_stage;
     p.kp = std::max(32, next_pow2(std::max(1, ctx->th.max_peaks)));
-    p.seg_cl = cl_entries_for(ctx, l.word_rows, l.hit_stage, l.ctas_per_sm, l.threads) /
-               (l.threads / 32);
+    // the list area: a sixth (at least one entry per thread) for the
+    // gathered entries of the check (larger lists are gathered in rounds),
+    // the rest split into per-warp lists, half of each (a multiple of 32)
+    // being the warp's overflow area: a lane's column overflows when its
+    // word row is crossed by many more lines than the average row
+    const int cl = cl_entries_for(ctx, l.word_rows, l.hit_stage, l.ctas_per_sm, l.threads);
+    p.cl_total = cl;
+    p.cmp_cap = std::max(l.threads, cl / 6 / l.threads * l.threads);
+    p.seg_cl = (cl - p.cmp_cap) / (l.threads / 32);
+    p.seg_ovf = (p.seg_cl / 2) & ~31;
     return p;
 }
 

@@ -45,6 +45,7 @@
 namespace hk {
 
 constexpr int kSegPk = 64;      // peak-key segment per warp; merged when past 32 entries
+constexpr int kMergeStage = 4 * HOUGH_MAX_PEAKS * 4 / 8;   // merge staging keys (the pk area)
 constexpr unsigned long long kKeyMax = ~0ull;
 
 struct KParams {
@@ -85,12 +86,15 @@ struct KParams {
     unsigned nrho_inv;  // ceil(2^32 / n_rho): word-column index -> row group
     int hit_stage;      // HS
     int kp;             // top-k region (power of two >= max(32, max_peaks))
+    int cl_total;       // entries of the list area (the host sized shared memory with it)
     int seg_cl;         // candidate-list entries per warp
+    int seg_ovf;        // of which the warp's shared overflow area
+    int cmp_cap;        // gathered-entry area after the lists (a multiple of blockDim)
 };
 
 // Shared-memory carve-up shared by host (size) and device (pointers).
 struct SmemLayout {
-    size_t acc, stage, carry, keys, cl, pk, cnt, hist, vh, pre, wtot, total;
+    size_t acc, stage, carry, keys, cl, pk, cnt, hist, vh, wtot, total;
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -115,11 +119,9 @@ __host__ __device__ inline SmemLayout smem_layout(int word_rows, int hit_stage, 
     L.cnt = off;                                    // counts + cursors per category
     off = align_up(off + (size_t)2 * (HOUGH_MAX_PEAKS + 2) * 4, 16);
     L.hist = off;                                   // per-warp counters (WarpCounters)
-    off = align_up(off + (size_t)5 * 32 * 4, 16);
+    off = align_up(off + (size_t)6 * 32 * 4, 16);
     L.vh = off;                                     // per-warp peak-vote histograms
     off = align_up(off + (size_t)n_warps * 64 * 4, 16);
-    L.pre = off;                                    // per-thread list prefix
-    off = align_up(off + (size_t)n_warps * 32 * 4, 16);
     L.wtot = off;
     off = align_up(off + 32 * 4, 16);
     L.total = off;
@@ -145,6 +147,7 @@ struct WarpCounters {
     int *pre_cl;    // exclusive prefix of n_cl (spreading the check over warps)
     int *pre_pk;    // exclusive prefix of n_pk (merging); separate from pre_cl
                     // because a merge can run in the middle of the check
+    int *n_ovf;     // entries the warp's lanes sent to its overflow area in this tile
 };
 
 __device__ __forceinline__ unsigned lanemask_lt()
@@ -225,13 +228,35 @@ __device__ int stage_hits(const KParams &p, long long base, int n, int2 *stage, 
 // A vote whose atomic returns T - 1 made its bin reach T (exactly once per
 // such bin): the bin is listed in the lane's own column of the warp's list,
 // seg[slot * 32 + lane], as (word index << 2) | field, cnt being the lane's
-// register count (no shared counter, no warp vote).  cnt may pass L: then
-// only the first L entries were stored.  FAST: the host proved that every
+// register count (no shared counter, no warp vote).  A lane whose column is
+// full (cnt >= L) appends to the warp's overflow area instead (list_append).  FAST: the host proved that every
 // valid hit votes in range, and the tile has no row past n_theta, so the
 // per-vote checks are left out.
+// Per-warp candidate list: L column slots per lane (seg[slot * 32 + lane]),
+// then an overflow area of p.seg_ovf entries shared by the warp's lanes
+// (seg[L * 32 + j], j from the warp's counter *ovf).  Overflow is rare, so
+// its shared counter is seldom contended.
+struct ListOvf {
+    int *count;   // the warp's overflow counter
+    int cap;      // overflow-area entries
+};
+
+__device__ __forceinline__ void list_append(uint32_t *seg, int L, int &cnt, const ListOvf &ovf,
+                                            uint32_t e)
+{
+    if (cnt < L) {
+        seg[cnt * 32 + (threadIdx.x & 31)] = e;
+        ++cnt;
+    } else {
+        const int j = atomicAdd(ovf.count, 1);
+        if (j < ovf.cap)
+            seg[L * 32 + j] = e;
+    }
+}
+
 template <int P, bool FAST>
 __device__ void vote_tile(const KParams &p, uint32_t *acc, const int2 *stage, int nh, int t0,
-                          uint32_t *seg, int L, int &cnt, WinScalars &ws)
+                          uint32_t *seg, int L, int &cnt, const ListOvf &ovf, WinScalars &ws)
 {
     constexpr int CW = 32 / P;
     constexpr unsigned MASK = P == 1 ? 0xffffffffu : ((1u << CW) - 1u);
@@ -268,11 +293,8 @@ __device__ void vote_tile(const KParams &p, uint32_t *acc, const int2 *stage, in
                 oor |= act[k] && !in;
             }
             const unsigned old = in ? atom_add_shared(col + (unsigned)b * 128u, 1u << (k * CW)) : 0u;
-            if (in && ((old >> (k * CW)) & MASK) == tm1) {
-                if (cnt < L)
-                    seg[cnt * 32 + lane] = ((col_word0 + (unsigned)b * 32u) << 2) | (unsigned)k;
-                ++cnt;
-            }
+            if (in && ((old >> (k * CW)) & MASK) == tm1)
+                list_append(seg, L, cnt, ovf, ((col_word0 + (unsigned)b * 32u) << 2) | (unsigned)k);
         }
     }
     if (oor)
@@ -331,9 +353,36 @@ struct TileView {
     // Section 4/5 peak rule: > earlier neighbours (row-major), >= later ones.
     __device__ __forceinline__ bool is_peak(int t, int b, int v) const
     {
+        const int i = t - t0;
+        if (i >= 1 && i + 1 < R && t + 1 < n_theta && b >= 1 && b + 1 < n_rho)
+            return is_peak_inside(i, b, v);
         const int a0 = get(t - 1, b - 1), a1 = get(t - 1, b), a2 = get(t - 1, b + 1);
         const int a3 = get(t, b - 1), a4 = get(t, b + 1);
         const int a5 = get(t + 1, b - 1), a6 = get(t + 1, b), a7 = get(t + 1, b + 1);
+        const int earlier = max(max(a0, a1), max(a2, a3));
+        const int later = max(max(a4, a5), max(a6, a7));
+        return v > earlier && v >= later;
+    }
+
+    // Word index of tile row i at bin b, and the shift of its field.
+    __device__ __forceinline__ int row_word(int i, int b, int &sh) const
+    {
+        const int wr = i & ((1 << lw) - 1);
+        sh = (i >> lw) * (32 / P);
+        return ((wr >> 5) * n_rho + b) * 32 + (wr & 31);
+    }
+
+    // The same rule for a bin whose eight neighbours all lie in the tile:
+    // three row bases, then eight plain loads (no clamping or selection).
+    __device__ __forceinline__ bool is_peak_inside(int i, int b, int v) const
+    {
+        constexpr unsigned MASK = P == 1 ? 0xffffffffu : ((1u << (32 / P)) - 1u);
+        int sa, sb, sc;
+        const int wa = row_word(i - 1, b, sa), wb = row_word(i, b, sb), wc = row_word(i + 1, b, sc);
+        const int a0 = (int)((acc[wa - 32] >> sa) & MASK), a1 = (int)((acc[wa] >> sa) & MASK);
+        const int a2 = (int)((acc[wa + 32] >> sa) & MASK), a3 = (int)((acc[wb - 32] >> sb) & MASK);
+        const int a4 = (int)((acc[wb + 32] >> sb) & MASK), a5 = (int)((acc[wc - 32] >> sc) & MASK);
+        const int a6 = (int)((acc[wc] >> sc) & MASK), a7 = (int)((acc[wc + 32] >> sc) & MASK);
         const int earlier = max(max(a0, a1), max(a2, a3));
         const int later = max(max(a4, a5), max(a6, a7));
         return v > earlier && v >= later;
@@ -438,19 +487,14 @@ __device__ __forceinline__ uint32_t field_flags(uint32_t w, const ScanTest &k)
 // every blockDim-th bin.
 template <int P>
 __device__ void list_carry(const KParams &p, const TileView<P> &tv, int rlo, int rhi,
-                           uint32_t *seg, int L, int &cnt)
+                           uint32_t *seg, int L, int &cnt, const ListOvf &ovf)
 {
-    const int lane = threadIdx.x & 31;
     const int tc = tv.t0 - 1;
     if (!(tc >= 0 && tc >= rlo && tc < rhi))
         return;
-    for (int b = threadIdx.x; b < p.n_rho; b += blockDim.x) {
-        if (tv.carry1[b] >= p.T) {
-            if (cnt < L)
-                seg[cnt * 32 + lane] = 0x80000000u | (unsigned)b;
-            ++cnt;
-        }
-    }
+    for (int b = threadIdx.x; b < p.n_rho; b += blockDim.x)
+        if (tv.carry1[b] >= p.T)
+            list_append(seg, L, cnt, ovf, 0x80000000u | (unsigned)b);
 }
 
 // Book-keeping of the peaks a warp found in one step (all lanes call): count
@@ -473,7 +517,9 @@ __device__ __forceinline__ void record_peaks(bool peak, int v, int t, int b, Pea
     if (m == 0u)
         return;
     ps.found += __popc(m);
-    if (peak && ps.hist)
+    // vote counts below the current bound vk can never again decide it (vk
+    // only rises), so only peaks with >= vk votes are counted
+    if (peak && ps.hist && v >= ps.vk)
         atomicAdd(ps.hist + min(v, kHistBins - 1), 1);   // this warp's own row
     const unsigned long long key = make_key(v, t, b);
     const bool app = peak && key < ps.kth && v >= ps.vk;
@@ -599,32 +645,60 @@ __device__ void merge_peaks(const KParams &p, unsigned long long *keys,
     const int m = ws.n_sel;
     const int keep = min(p.max_peaks, m);
     const unsigned long long *segs = keys + p.kp;
-    for (int idx = threadIdx.x; idx < m; idx += blockDim.x) {
-        unsigned long long x;
-        if (idx < n_top) {
-            x = keys[idx];
-        } else {
-            int k = 0;
-            while (k + 1 < nw && wc.pre_pk[k + 1] <= idx)
-                ++k;
-            x = segs[(size_t)k * seg_cap + (idx - wc.pre_pk[k])];
+    // entry idx of the virtual list: the kept prefix, then the segments
+    auto entry = [&](int idx) {
+        if (idx < n_top)
+            return keys[idx];
+        int k = 0;
+        while (k + 1 < nw && wc.pre_pk[k + 1] <= idx)
+            ++k;
+        return segs[(size_t)k * seg_cap + (idx - wc.pre_pk[k])];
+    };
+    if (m <= kMergeStage) {
+        // gather the entries into one array, then rank each against all
+        // (keys are distinct: its rank is its place) and write the best
+        // `keep` straight into the kept list
+        for (int idx = threadIdx.x; idx < m; idx += blockDim.x)
+            top_stage[idx] = entry(idx);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < m; idx += blockDim.x) {
+            const unsigned long long x = top_stage[idx];
+            int r0 = 0, r1 = 0, r2 = 0, r3 = 0;
+            int y = 0;
+            for (; y + 4 <= m; y += 4) {
+                r0 += top_stage[y] < x ? 1 : 0;
+                r1 += top_stage[y + 1] < x ? 1 : 0;
+                r2 += top_stage[y + 2] < x ? 1 : 0;
+                r3 += top_stage[y + 3] < x ? 1 : 0;
+            }
+            for (; y < m; ++y)
+                r0 += top_stage[y] < x ? 1 : 0;
+            const int rank = r0 + r1 + r2 + r3;
+            if (rank < keep)
+                keys[rank] = x;
         }
-        int rank = 0;
-        for (int y = 0; y < n_top; ++y)
-            rank += keys[y] < x ? 1 : 0;
-        for (int k = 0; k < nw; ++k) {
-            const unsigned long long *sg = segs + (size_t)k * seg_cap;
-            const int c = wc.n_pk[k];
+        for (int i = keep + threadIdx.x; i < p.kp; i += blockDim.x)
+            keys[i] = kKeyMax;
+    } else {
+        for (int idx = threadIdx.x; idx < m; idx += blockDim.x) {
+            const unsigned long long x = entry(idx);
+            int rank = 0;
+            for (int y = 0; y < n_top; ++y)
+                rank += keys[y] < x ? 1 : 0;
+            for (int k = 0; k < nw; ++k) {
+                const unsigned long long *sg = segs + (size_t)k * seg_cap;
+                const int c = wc.n_pk[k];
 #pragma unroll 4
-            for (int y = 0; y < c; ++y)
-                rank += sg[y] < x ? 1 : 0;
+                for (int y = 0; y < c; ++y)
+                    rank += sg[y] < x ? 1 : 0;
+            }
+            if (rank < keep)
+                top_stage[rank] = x;
         }
-        if (rank < keep)
-            top_stage[rank] = x;
+        __syncthreads();
+        for (int i = threadIdx.x; i < p.kp; i += blockDim.x)
+            keys[i] = i < keep ? top_stage[i] : kKeyMax;
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < p.kp; i += blockDim.x)
-        keys[i] = i < keep ? top_stage[i] : kKeyMax;
     if (lane == 0)
         wc.n_pk[warp] = 0;
     __syncthreads();
@@ -707,11 +781,13 @@ __device__ void check_direct(const KParams &p, const TileView<P> &tv, int rlo, i
     }
 }
 
+// Returns the number of valid hits left in `stage` (in their original order),
+// or -1 when the window was streamed through the stage in parts.
 template <int P>
-__device__ void process_tiles(const KParams &p, long long beg, int H, uint32_t *acc, int2 *stage,
+__device__ int process_tiles(const KParams &p, long long beg, int H, uint32_t *acc, int2 *stage,
                               int *carry, unsigned long long *keys, uint32_t *cl,
                               unsigned long long *top_stage, WarpCounters wc, int *vh,
-                              int *pre_thr, int *wtot, WinScalars &ws, long long w)
+                              int *wtot, WinScalars &ws, long long w)
 {
     const int WR = p.word_rows;
     const int R = WR * P;
@@ -722,6 +798,7 @@ __device__ void process_tiles(const KParams &p, long long beg, int H, uint32_t *
     int *carry0 = carry, *carry1 = carry + p.n_rho;
     const int acc_words4 = (WR * p.n_rho) >> 2;
     uint32_t *my_cl = cl + (size_t)warp * p.seg_cl;
+    uint32_t *cmp = cl + (size_t)nw * p.seg_cl;     // the gathered entries
     (void)lane;
 
     int nv = 0;
@@ -734,20 +811,23 @@ __device__ void process_tiles(const KParams &p, long long beg, int H, uint32_t *
         uint4 *acc4 = reinterpret_cast<uint4 *>(acc);
         for (int i = threadIdx.x; i < acc_words4; i += blockDim.x)
             acc4[i] = make_uint4(0u, 0u, 0u, 0u);
+        if (threadIdx.x < 32)
+            wc.n_ovf[threadIdx.x] = 0;
         __syncthreads();
-        int cnt = 0;        // this lane's candidate count (a register)
-        const int L = p.seg_cl >> 5;
+        int cnt = 0;        // this lane's column entries (a register)
+        const int L = (p.seg_cl - p.seg_ovf) >> 5;
+        const ListOvf ovf{wc.n_ovf + warp, p.seg_ovf};
         const bool fast = p.in_range && t0 + R <= p.n_theta;
         if (single) {
             if (fast)
-                vote_tile<P, true>(p, acc, stage, nv, t0, my_cl, L, cnt, ws);
+                vote_tile<P, true>(p, acc, stage, nv, t0, my_cl, L, cnt, ovf, ws);
             else
-                vote_tile<P, false>(p, acc, stage, nv, t0, my_cl, L, cnt, ws);
+                vote_tile<P, false>(p, acc, stage, nv, t0, my_cl, L, cnt, ovf, ws);
         } else {
             for (long long s0 = 0; s0 < H; s0 += p.hit_stage) {
                 int n = (int)min((long long)p.hit_stage, (long long)H - s0);
                 int ns = stage_hits(p, beg + s0, n, stage, wtot, ws);
-                vote_tile<P, false>(p, acc, stage, ns, t0, my_cl, L, cnt, ws);
+                vote_tile<P, false>(p, acc, stage, ns, t0, my_cl, L, cnt, ovf, ws);
                 __syncthreads();
             }
         }
@@ -760,11 +840,17 @@ __device__ void process_tiles(const KParams &p, long long beg, int H, uint32_t *
         const int rlo = max(t0 - 1, 0);
         const int rhi = last ? p.n_theta : t0 + R - 1;
         const int ihi = rhi - t0;
-        list_carry<P>(p, tv, rlo, rhi, my_cl, L, cnt);
-        // block-wide exclusive prefix of the lanes' counts (list overflow: any
-        // count past L sends the tile to the direct test)
+        list_carry<P>(p, tv, rlo, rhi, my_cl, L, cnt, ovf);
+        __syncthreads();
+        // block-wide exclusive prefix of the lanes' counts; lane 31 also owns
+        // its warp's overflow entries (only an overflow area past its
+        // capacity sends the tile to the direct test)
+        int my_n = 0, my_pre = 0;   // this thread's entries and their first index
         {
-            const int c = min(cnt, L);
+            const int n_ovf = wc.n_ovf[warp];
+            int c = cnt;
+            if (lane == 31)
+                c += min(n_ovf, p.seg_ovf);
             int incl = c;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
@@ -774,7 +860,7 @@ __device__ void process_tiles(const KParams &p, long long beg, int H, uint32_t *
             }
             if (lane == 31)
                 wc.n_cl[warp] = incl;
-            const bool ovf = __syncthreads_or(cnt > L);
+            const bool lost = __syncthreads_or(lane == 0 && n_ovf > p.seg_ovf);
             if (warp == 0) {
                 const int wt = lane < nw ? wc.n_cl[lane] : 0;
                 int wi = wt;
@@ -788,43 +874,56 @@ __device__ void process_tiles(const KParams &p, long long beg, int H, uint32_t *
                     wc.pre_cl[lane] = wi - wt;
                 if (lane == 31) {
                     ws.n_sel = wi;
-                    ws.seg_ovf = ovf ? 1 : 0;
+                    ws.seg_ovf = lost ? 1 : 0;
                 }
             }
             __syncthreads();
-            pre_thr[threadIdx.x] = wc.pre_cl[warp] + incl - c;
-            __syncthreads();
+            my_n = c;
+            my_pre = wc.pre_cl[warp] + incl - c;
         }
         PeakSink ps{keys + p.kp + (size_t)warp * seg_cap, seg_cap, wc.n_pk[warp], 0, ws.kth,
                     ws.vk, vh + warp * kHistBins};
         if (!ws.seg_ovf) {
-            // one thread per listed candidate, spread over all warps
+            // One thread per listed entry, all warps evenly loaded.  The
+            // entries are first gathered into cmp in a transposed order:
+            // within each block-sized chunk, entry y of the compact order
+            // (owner-major) goes to slot (y % nw) * 32 + y / nw, so that the
+            // lanes of a warp read consecutive slots (no bank conflict) that
+            // hold entries of 32 different owners, whose word rows, and so
+            // whose tile banks, differ.  cmp holds p.cmp_cap entries; larger
+            // lists are taken in rounds.
             const int total = ws.n_sel;
-            for (int x0 = 0; x0 < total; x0 += blockDim.x) {
-                const int x = x0 + threadIdx.x;
-                bool peak = false;
-                int v = 0, i = 0, b = 0;
-                if (x < total) {
-                    // the thread (warp, lane) whose column holds entry x
-                    int u = 0;
-#pragma unroll 1
-                    for (int step = 512; step > 0; step >>= 1)
-                        if (u + step < (int)blockDim.x && pre_thr[u + step] <= x)
-                            u += step;
-                    const int slot = x - pre_thr[u];
-                    const uint32_t e = cl[(size_t)(u >> 5) * p.seg_cl + slot * 32 + (u & 31)];
-                    decode_entry<P>(p, tv, e, v, i, b);
-                    peak = i < ihi && v >= p.T && tv.is_peak(t0 + i, b, v);
+            const int B = blockDim.x, lnw = __ffs(nw) - 1;
+            for (int base = 0; base < total; base += p.cmp_cap) {
+                const int hi = min(total - base, p.cmp_cap);
+                for (int j = 0; j < my_n; ++j) {
+                    const int y = my_pre + j - base;
+                    if (y >= 0 && y < hi) {
+                        const uint32_t e = j < cnt ? my_cl[j * 32 + lane] : my_cl[L * 32 + (j - cnt)];
+                        const int yl = y & (B - 1);
+                        cmp[(y - yl) + ((yl & (nw - 1)) << 5) + (yl >> lnw)] = e;
+                    }
                 }
-                record_peaks(peak, v, t0 + i, b, ps);
-                if (lane == 0)
-                    wc.n_pk[warp] = ps.n;
-                if (__syncthreads_or(lane == 0 && ps.n > seg_cap - 32)) {
-                    merge_peaks(p, keys, top_stage, seg_cap, wc, vh, ws);
-                    ps.n = 0;
-                    ps.kth = ws.kth;
-                    ps.vk = ws.vk;
+                __syncthreads();
+                for (int c0 = 0; c0 < hi; c0 += B) {
+                    const int y = c0 + (lane << lnw) + warp;
+                    bool peak = false;
+                    int v = 0, i = 0, b = 0;
+                    if (y < hi) {
+                        decode_entry<P>(p, tv, cmp[c0 + threadIdx.x], v, i, b);
+                        peak = i < ihi && v >= p.T && tv.is_peak(t0 + i, b, v);
+                    }
+                    record_peaks(peak, v, t0 + i, b, ps);
+                    if (lane == 0)
+                        wc.n_pk[warp] = ps.n;
+                    if (__syncthreads_or(lane == 0 && ps.n > seg_cap - 32)) {
+                        merge_peaks(p, keys, top_stage, seg_cap, wc, vh, ws);
+                        ps.n = 0;
+                        ps.kth = ws.kth;
+                        ps.vk = ws.vk;
+                    }
                 }
+                __syncthreads();
             }
         } else {
             check_direct<P>(p, tv, rlo, rhi, ps, keys, top_stage, seg_cap, wc, vh, ws);
@@ -849,13 +948,22 @@ __device__ void process_tiles(const KParams &p, long long beg, int H, uint32_t *
         pending += wc.n_pk[k];
     if (pending > 0)
         merge_peaks(p, keys, top_stage, seg_cap, wc, vh, ws);
+    return single ? nv : -1;
 }
-// Step D: first matching peak in order, then per-peak compaction.  Warp 0
-// counts the categories and scatters; no other warp touches the counters.
+// Step D: first matching peak in order, then the stable per-peak compaction.
+// Categories: peak index q < n_top, n_top for a hit on no peak's line,
+// n_top + 1 for a hit outside the detector box.  hits_s: the window's hits
+// in shared memory when every one of them is valid (else NULL: read from
+// global memory); cat_s: room for H categories in shared memory (else NULL:
+// re-read from hit_track).  Each warp compacts its own contiguous slice of
+// the hits: it counts its categories (wcat, one row per warp), a prefix over
+// categories and then over warps gives every (warp, category) its first
+// slot, and the warp scatters its slice in order.
 __device__ void associate(const KParams &p, long long w, long long beg, int H, int n_top,
-                          const unsigned long long *keys, int *pk, int *cnt, int *cursor,
-                          int *cat_s, bool cat_in_smem)
+                          const unsigned long long *keys, int *pk, const int2 *hits_s,
+                          int *cat_s, int *wcat, int *cat_base)
 {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     int *pk_t = pk, *pk_b = pk + HOUGH_MAX_PEAKS, *pk_c = pk + 2 * HOUGH_MAX_PEAKS,
         *pk_s = pk + 3 * HOUGH_MAX_PEAKS;
     for (int i = threadIdx.x; i < n_top; i += blockDim.x) {
@@ -866,6 +974,9 @@ __device__ void associate(const KParams &p, long long w, long long beg, int H, i
         pk_c[i] = __ldg(p.C + t);
         pk_s[i] = __ldg(p.S + t);
     }
+    const int NC = n_top + 2;
+    for (int q = threadIdx.x; q < nw * NC; q += blockDim.x)
+        wcat[q] = 0;
     __syncthreads();
     const int D = p.D, K = p.K;
     const int tol = p.tol;
@@ -877,7 +988,17 @@ __device__ void associate(const KParams &p, long long w, long long beg, int H, i
         const int i = i0 + (int)(threadIdx.x >> 2);
         int phi = 0, z = 0;
         const bool in = i < H;
-        const bool ok = in && load_hit(p, beg + i, phi, z);
+        bool ok = false;
+        if (in) {
+            if (hits_s) {
+                const int2 h = hits_s[i];
+                phi = h.x;
+                z = h.y;
+                ok = true;
+            } else {
+                ok = load_hit(p, beg + i, phi, z);
+            }
+        }
         int first = n_top;
         if (ok) {
             for (int q = sub; q < n_top; q += 4) {
@@ -893,84 +1014,86 @@ __device__ void associate(const KParams &p, long long w, long long beg, int H, i
         if (in && sub == 0) {
             const int cat = ok ? first : n_top + 1;
             p.hit_track[beg + i] = cat < n_top ? cat : (cat == n_top ? -1 : -2);
-            if (cat_in_smem)
+            if (cat_s)
                 cat_s[i] = cat;
         }
     }
     __syncthreads();
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        for (int q = lane; q < n_top + 2; q += 32)
-            cnt[q] = 0;
+    auto category = [&](int i) {
+        if (cat_s)
+            return cat_s[i];
+        const int v = p.hit_track[beg + i];
+        return v >= 0 ? v : (v == -1 ? n_top : n_top + 1);
+    };
+    const int chunk = (H + nw - 1) / nw;
+    const int h0 = min(H, warp * chunk), h1 = min(H, h0 + chunk);
+    int *mine = wcat + warp * NC;
+    for (int base = h0; base < h1; base += 32) {
+        const int i = base + lane;
+        const int cat = i < h1 ? category(i) : -1;
+        const unsigned m = __match_any_sync(0xffffffffu, cat);
+        if (i < h1 && lane == __ffs(m) - 1)
+            mine[cat] += __popc(m);          // leaders of distinct categories
         __syncwarp();
-        for (int base = 0; base < H; base += 32) {
-            const int i = base + lane;
-            int cat = -1;
-            if (i < H) {
-                if (cat_in_smem) {
-                    cat = cat_s[i];
-                } else {
-                    int v = p.hit_track[beg + i];
-                    cat = v >= 0 ? v : (v == -1 ? n_top : n_top + 1);
-                }
-            }
-            const unsigned m = __match_any_sync(0xffffffffu, cat);
-            if (i < H && lane == __ffs(m) - 1)
-                cnt[cat] += __popc(m);
-            __syncwarp();
-        }
+    }
+    __syncthreads();
+    if (warp == 0) {
         int run = 0;
-        for (int base = 0; base < n_top + 2; base += 32) {
-            int q = base + lane;
-            int c = q < n_top + 2 ? cnt[q] : 0;
-            int incl = c;
+        for (int b0 = 0; b0 < NC; b0 += 32) {
+            const int q = b0 + lane;
+            int tot = 0;
+            if (q < NC)
+                for (int k = 0; k < nw; ++k)
+                    tot += wcat[k * NC + q];
+            int incl = tot;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
-                int y = __shfl_up_sync(0xffffffffu, incl, d);
+                const int y = __shfl_up_sync(0xffffffffu, incl, d);
                 if (lane >= d)
                     incl += y;
             }
-            int excl = run + incl - c;
-            if (q < n_top + 2)
-                cursor[q] = excl;
+            const int excl = run + incl - tot;
+            if (q < NC)
+                cat_base[q] = excl;
             if (q < n_top) {
-                unsigned long long k = keys[q];
+                const unsigned long long k = keys[q];
                 hough_peak pr;
                 pr.theta = (uint16_t)((k >> 16) & 0xffffu);
                 pr.rho = (uint16_t)(k & 0xffffu);
                 pr.votes = (int32_t)key_votes(k);
-                pr.n_hits = c;
+                pr.n_hits = tot;
                 pr.hit_begin = excl;
                 p.peaks[(size_t)w * p.max_peaks + q] = pr;
             }
             run += __shfl_sync(0xffffffffu, incl, 31);
         }
-        __syncwarp();
-        for (int base = 0; base < H; base += 32) {
-            int i = base + lane;
-            bool in = i < H;
-            int cat = -1;
-            if (in) {
-                if (cat_in_smem) {
-                    cat = cat_s[i];
-                } else {
-                    int v = p.hit_track[beg + i];
-                    cat = v >= 0 ? v : (v == -1 ? n_top : n_top + 1);
-                }
-            }
-            unsigned m = __match_any_sync(0xffffffffu, cat);
-            int leader = __ffs(m) - 1;
-            int rank = __popc(m & lanemask_lt());
-            int pos = 0;
-            if (in && lane == leader) {
-                pos = cursor[cat];
-                cursor[cat] = pos + __popc(m);
-            }
-            pos = __shfl_sync(0xffffffffu, pos, leader);
-            if (in)
-                p.track_hits[beg + pos + rank] = i;
-            __syncwarp();
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < NC; q += blockDim.x) {
+        int run = cat_base[q];
+        for (int k = 0; k < nw; ++k) {
+            const int c = wcat[k * NC + q];
+            wcat[k * NC + q] = run;
+            run += c;
         }
+    }
+    __syncthreads();
+    for (int base = h0; base < h1; base += 32) {
+        const int i = base + lane;
+        const bool in = i < h1;
+        const int cat = in ? category(i) : -1;
+        const unsigned m = __match_any_sync(0xffffffffu, cat);
+        const int leader = __ffs(m) - 1;
+        const int rank = __popc(m & lanemask_lt());
+        int pos = 0;
+        if (in && lane == leader) {
+            pos = mine[cat];
+            mine[cat] = pos + __popc(m);
+        }
+        pos = __shfl_sync(0xffffffffu, pos, leader);
+        if (in)
+            p.track_hits[beg + pos + rank] = i;
+        __syncwarp();
     }
     __syncthreads();
 }
@@ -980,7 +1103,7 @@ __global__ void __launch_bounds__(1024, 1) find_kernel(KParams p)
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ WinScalars ws;
     const int nw = blockDim.x >> 5;
-    const SmemLayout L = smem_layout(p.word_rows, p.hit_stage, p.n_rho, p.seg_cl * nw, nw);
+    const SmemLayout L = smem_layout(p.word_rows, p.hit_stage, p.n_rho, p.cl_total, nw);
     uint32_t *acc = reinterpret_cast<uint32_t *>(smem + L.acc);
     int2 *stage = reinterpret_cast<int2 *>(smem + L.stage);
     int *carry = reinterpret_cast<int *>(smem + L.carry);
@@ -989,11 +1112,9 @@ __global__ void __launch_bounds__(1024, 1) find_kernel(KParams p)
     int *pk = reinterpret_cast<int *>(smem + L.pk);
     unsigned long long *top_stage = reinterpret_cast<unsigned long long *>(smem + L.pk);
     int *cnt = reinterpret_cast<int *>(smem + L.cnt);
-    int *cursor = cnt + (HOUGH_MAX_PEAKS + 2);
     int *wcnt = reinterpret_cast<int *>(smem + L.hist);
-    WarpCounters wc{wcnt, wcnt + 32, wcnt + 64, wcnt + 96, wcnt + 128};
+    WarpCounters wc{wcnt, wcnt + 32, wcnt + 64, wcnt + 96, wcnt + 128, wcnt + 160};
     int *vh = reinterpret_cast<int *>(smem + L.vh);
-    int *pre_thr = reinterpret_cast<int *>(smem + L.pre);
     int *wtot = reinterpret_cast<int *>(smem + L.wtot);
 
     long long w = blockIdx.x;
@@ -1026,17 +1147,29 @@ __global__ void __launch_bounds__(1024, 1) find_kernel(KParams p)
             for (int i = threadIdx.x; i < nw * kHistBins; i += blockDim.x)
                 vh[i] = 0;
             __syncthreads();
+            int nv;
             if (H <= 255)
-                process_tiles<4>(p, beg, H, acc, stage, carry, keys, cl, top_stage, wc, vh, pre_thr, wtot, ws, w);
+                nv = process_tiles<4>(p, beg, H, acc, stage, carry, keys, cl, top_stage, wc, vh, wtot, ws, w);
             else if (H <= 65535)
-                process_tiles<2>(p, beg, H, acc, stage, carry, keys, cl, top_stage, wc, vh, pre_thr, wtot, ws, w);
+                nv = process_tiles<2>(p, beg, H, acc, stage, carry, keys, cl, top_stage, wc, vh, wtot, ws, w);
             else
-                process_tiles<1>(p, beg, H, acc, stage, carry, keys, cl, top_stage, wc, vh, pre_thr, wtot, ws, w);
+                nv = process_tiles<1>(p, beg, H, acc, stage, carry, keys, cl, top_stage, wc, vh, wtot, ws, w);
             __syncthreads();
             const int n_top = ws.n_top;
-            const bool cat_in_smem = H <= 2 * p.hit_stage;
-            associate(p, w, beg, H, n_top, keys, pk, cnt, cursor, reinterpret_cast<int *>(stage),
-                      cat_in_smem);
+            // the tile and the list area are free now: the per-warp category
+            // counts go to the tile (else to the list area; the host made
+            // sure one of them is large enough), the categories to the list
+            // area when they fit
+            int *wcat, *cat_s;
+            const int need = nw * (n_top + 2);
+            if (need <= p.word_rows * p.n_rho) {
+                wcat = reinterpret_cast<int *>(acc);
+                cat_s = H <= p.cl_total ? reinterpret_cast<int *>(cl) : nullptr;
+            } else {
+                wcat = reinterpret_cast<int *>(cl);
+                cat_s = H + need <= p.cl_total ? reinterpret_cast<int *>(cl) + need : nullptr;
+            }
+            associate(p, w, beg, H, n_top, keys, pk, nv == H ? stage : nullptr, cat_s, wcat, cnt);
             if (threadIdx.x == 0) {
                 int found = 0;
                 for (int k = 0; k < nw; ++k)
