@@ -149,6 +149,66 @@ def _cpu_baseline(w, n_theta, n_rho, budget_s=12.0):
             "sample_single_core": f"first {n1} windows, 1 thread ({dt1:.1f} s)"}
 
 
+def _slicing_leg(args, dev, stream, flush, hbm_gbs):
+    """Time slicing on the device (Section 5: 10 ns windows sliding by 5 ns)
+    of a time-ordered stream, then the whole find over the sliced windows.
+    The stream: decays at --slice-rate per ns for --slice-us microseconds."""
+    import torch
+    from paper_2511_02742_gb300 import hough, synth
+    s = synth.timed_stream(args.slice_us * 1000.0, args.slice_rate, noise_frac=0.02, seed=5)
+    step, m = 5000, 2                                     # ps: 5 ns step, 10 ns windows
+    W = int(args.slice_us * 1000 * 1000 // step) + 1
+    f = hough.Finder(512, 512)
+    t = torch.from_numpy(s.t).to(dev)
+    hits = dict(vane=torch.from_numpy(s.vane).to(dev), strip=torch.from_numpy(s.strip).to(dev))
+    r = f.time_slice(t, hits, 0, step, m * step, W, stream=stream)
+    out = f.alloc_outputs(W, r["capacity"], device=dev)
+    for _ in range(3):
+        f.time_slice(t, hits, 0, step, m * step, W, stream=stream)
+        f.find(r["hits"], r["offsets"], out=out, stream=stream)
+    torch.cuda.synchronize()
+    steps = max(1, min(args.steps, 10))
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    for i in range(steps):
+        _flush_l2(flush)
+        ev[i][0].record(stream)
+        hough.hough_time_slice(f.ctx, t, hits["vane"], hits["strip"], 0, step, m * step, W,
+                               r["hits"]["vane"], r["hits"]["strip"], r["index"], r["offsets"],
+                               r["status"], stream)
+        ev[i][1].record(stream)
+        f.find(r["hits"], r["offsets"], out=out, stream=stream)
+        ev[i][2].record(stream)
+    torch.cuda.synchronize()
+    slice_ms = sum(a.elapsed_time(b) for a, b, _ in ev) / steps
+    chain_ms = sum(a.elapsed_time(c) for a, _, c in ev) / steps
+    total = int(r["offsets"][-1].item())
+    ok = int(r["status"].item()) == 0
+    n = s.n_hits
+    algo = 16 * n + 16 * total + 8 * (W + 1)              # t, in0/in1 read; out0/out1/index written
+    gbs = algo / (slice_ms * 1e-3) / 1e9
+    # parity of the timed slice on a sample of windows against the oracle
+    import oracle
+    offs = r["offsets"].cpu().numpy()
+    idx = r["index"].cpu().numpy()
+    lo, hi = W // 2, W // 2 + 40
+    sub = (s.t >= lo * step) & (s.t < (hi + m) * step)
+    first = int(np.argmax(sub)) if sub.any() else 0
+    o_ref, i_ref = oracle.time_slice(s.t[sub], lo * step, step, m * step, hi - lo)
+    same = all(np.array_equal(idx[offs[lo + k]:offs[lo + k + 1]],
+                              first + i_ref[o_ref[k]:o_ref[k + 1]]) for k in range(hi - lo))
+    f.close()
+    return {"workload": f"time-ordered stream: {args.slice_us:g} us at {args.slice_rate:g} decays/ns, "
+                        f"2% noise, {n} hits -> {W} windows of 10 ns sliding by 5 ns "
+                        f"({total} window-hits), 512x512",
+            "slice_ms": round(slice_ms, 4), "slice_hits_per_s": round(n / (slice_ms * 1e-3), 1),
+            "slice_then_find_ms": round(chain_ms, 4),
+            "slice_then_find_windows_per_s": round(W / (chain_ms * 1e-3), 1),
+            "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_gbs, "unit": "GB/s",
+                         "frac": round(gbs / hbm_gbs, 4) if hbm_gbs else None,
+                         "algorithmic_bytes": algo},
+            "sorted": ok, "parity_sample": {"windows": hi - lo, "equal": bool(same)}}
+
+
 def _serving_leg(args, dev):
     """Serving workload through the library's request loop (host buffers).
 
@@ -287,6 +347,22 @@ def run_reference(args):
 
 def _flush_l2(buf):
     buf.add_(1)
+
+
+def _recorded_traffic(workload, n_windows):
+    """DRAM bytes per launch of find_kernel from the committed ncu summary, if
+    that capture was of the kernel source as it is now (else None)."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "find_kernel_batched.traffic.json")
+    src = os.path.join(ROOT, "paper_2511_02742_gb300", "csrc", "hough_kernels.cuh")
+    if workload != "batched" or not os.path.exists(p):
+        return None, "no capture of this workload"
+    d = json.load(open(p))
+    if d.get("kernel_source_sha256") != hashlib.sha256(open(src, "rb").read()).hexdigest():
+        return None, "kernel changed since the capture"
+    scaled = d["measured_dram_bytes"] * n_windows / d["measured_windows"]
+    return int(round(scaled)), (f"ncu dram__bytes_read+write on {d['measured_windows']} windows, "
+                                f"scaled to {n_windows} (profiles/find_kernel_batched.traffic.json)")
 
 
 def _export_leg(args, dev, stream, flush, hbm_gbs):
@@ -477,9 +553,12 @@ def run_ours(args):
         if os.path.exists(pp):
             peaks_meas = json.load(open(pp))
         smem_peak = _smem_atomic_peak_gops(args)
+        traffic = _recorded_traffic(args.workload, w.n_windows)
         export = _export_leg(args, dev, stream, flush, peaks_meas.get("hbm_gbs")) \
             if args.export_windows > 0 else None
         serving = _serving_leg(args, dev) if args.serve_seconds > 0 else None
+        slicing = _slicing_leg(args, dev, stream, flush, peaks_meas.get("hbm_gbs")) \
+            if args.slice_us > 0 else None
         result = {
             "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
@@ -495,7 +574,8 @@ def run_ours(args):
                          "peak": smem_peak["value"], "unit": "Gvote/s",
                          "frac": round(ach_votes / 1e9 / smem_peak["value"], 4)
                          if smem_peak["value"] else None,
-                         "traffic": None, "peak_source": smem_peak["source"],
+                         "traffic": traffic[0], "traffic_source": traffic[1],
+                         "peak_source": smem_peak["source"],
                          "algorithmic": f"{votes} shared-memory vote atomics per launch "
                                         f"(valid hits x n_theta)",
                          "hbm": {"achieved_gbs": round(algo_bytes / (ms * 1e-3) / 1e9, 2),
@@ -506,6 +586,7 @@ def run_ours(args):
                                  "algorithmic_bytes": algo_bytes}},
             "roofline_export": export,
             "serving": serving,
+            "time_slicing": slicing,
             "latency_us": {"p50": serving["p50_us"], "p99": serving["p99_us"],
                            "source": "serving leg"} if serving else None,
             "cpu_baseline": cpu,
@@ -560,6 +641,8 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=1e5)
     ap.add_argument("--serve-slice-ms", type=float, default=1.0)
     ap.add_argument("--serve-pool", type=int, default=20000)
+    ap.add_argument("--slice-us", type=float, default=100.0)
+    ap.add_argument("--slice-rate", type=float, default=0.6)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the library's default launch shape instead of autotuning it")
     ap.add_argument("--no-probe", action="store_true")

@@ -214,6 +214,39 @@ int hough_find(hough_ctx *ctx, const hough_hits *hits, const int64_t *window_off
                int64_t n_windows, const hough_tracks *tracks_out, void *stream);
 
 /*
+ * Time slicing on the device (Section 5: the hits of a readout are divided
+ * into overlapping time windows of 10 ns with a sliding step of 5 ns;
+ * Section 6: each window is one unit of work).  Window k, 0 <= k < n_windows,
+ * holds every hit h with
+ *     t0 + k*step <= t[h] < t0 + k*step + len,
+ * in input order; a hit appears once in every window that covers its time.
+ *   t[n_hits]          device, int64 times (any unit), non-decreasing (a
+ *                      readout in time order);
+ *   in0/in1[n_hits]    device, the hits' (vane, strip) or (phi_q, z_q);
+ *   len                a multiple of step, at most HOUGH_SLICE_MAX_OVERLAP
+ *                      steps (the paper's windows are two steps long).
+ * Writes on the device, window by window:
+ *   window_offsets[n_windows + 1]   CSR offsets into the outputs;
+ *   out0/out1[...]                  in0/in1 of each window's hits;
+ *   out_index[...]                  the hits' input positions (may be NULL).
+ * out_capacity (entries of out0/out1/out_index) must be at least
+ * n_hits * (len / step), the most any input can need.  The result feeds
+ * hough_find as it is: hits (out0, out1) with n_hits = out_capacity, the same
+ * window_offsets and n_windows.  *status (device, may be NULL) is cleared and
+ * then receives HOUGH_SLICE_UNSORTED if t decreases anywhere (the outputs are
+ * then unspecified, but nothing outside the given arrays is touched).
+ * Asynchronous on stream.
+ * Errors: INVALID_ARG, UNSUPPORTED_SHAPE (len not a multiple of step or
+ * longer than HOUGH_SLICE_MAX_OVERLAP steps), CUDA.
+ */
+#define HOUGH_SLICE_MAX_OVERLAP 16
+#define HOUGH_SLICE_UNSORTED 1u
+int hough_time_slice(hough_ctx *ctx, const int64_t *t, const int32_t *in0, const int32_t *in1,
+                     int64_t n_hits, int64_t t0, int64_t step, int64_t len, int64_t n_windows,
+                     int32_t *out0, int32_t *out1, int64_t *out_index, int64_t out_capacity,
+                     int64_t *window_offsets, uint32_t *status, void *stream);
+
+/*
  * hough_find on HOST buffers: the same arguments, but every pointer in hits,
  * window_offsets and tracks_out is a host pointer.  The library copies inputs
  * to device staging buffers it owns, runs the path, copies the results back

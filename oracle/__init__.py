@@ -79,6 +79,8 @@ def _load():
         lib.oracle_find_window.restype = i32
         lib.oracle_find_batch.argtypes = [P, i32, i32, P, P, P, P, i64, P, P, P, P, P, P, P]
         lib.oracle_find_batch.restype = i32
+        lib.oracle_time_slice.argtypes = [P, i64, i64, i64, i64, i64, P, P, i64]
+        lib.oracle_time_slice.restype = i64
         _lib = lib
     return _lib
 
@@ -221,3 +223,19 @@ def find_batch(geom: dict, n_theta: int, n_rho: int, phi_q, z_q, offsets, vote_t
     return dict(acc=acc, peaks=pk.reshape(nw, max_peaks) if max_peaks else pk.reshape(nw, 0),
                 n_peaks=n_peaks, n_found=n_found, hit_track=hit_track, track_hits=track_hits,
                 status=status)
+
+
+def time_slice(t, t0: int, step: int, length: int, n_windows: int):
+    """Overlapping time windows (Section 5): (offsets int64[n_windows+1],
+    index int64[m]) -- window k holds the input positions of the hits with
+    t0 + k*step <= t < t0 + k*step + length, in input order."""
+    lib = _load()
+    t = np.ascontiguousarray(t, np.int64)
+    offsets = np.zeros(n_windows + 1, np.int64)
+    cap = max(1, len(t) * (-(-length // step)))
+    index = np.zeros(cap, np.int64)
+    m = lib.oracle_time_slice(_ptr(t), len(t), t0, step, length, n_windows, _ptr(offsets),
+                              _ptr(index), cap)
+    if m < 0:
+        raise ValueError(f"oracle_time_slice: error {m}")
+    return offsets, index[:m].copy()

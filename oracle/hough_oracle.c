@@ -26,6 +26,8 @@
  *      it lies on within the tolerance, |b_h(t_p) - b_p| <= tol (Section 5,
  *      seed hits "that align with the straight line"); then the hits are
  *      grouped per peak.
+ * and, before all of these, the time slicing of a readout into overlapping
+ * windows (Section 5: 10 ns windows sliding by 5 ns; oracle_time_slice).
  * The readings of the points the paper leaves open (units, theta sampling,
  * fixed-point tables, threshold, tie-break, tolerance) are listed in the
  * design notes of the repository.
@@ -33,7 +35,8 @@
  * Parity pins: tests/test_oracle_pins.py checks this file against brute force
  * on hand-built cases, the single-line closed form, the helix closed form,
  * the FP64 continuous definition (|b_fixed - b_fp64| <= 1), conservation of
- * votes and permutation invariance.
+ * votes and permutation invariance; tests/test_slicing_pins.py checks the
+ * time slicing against a hand-worked example and the closed-form membership.
  */
 #include <math.h>
 #include <stdint.h>
@@ -446,4 +449,41 @@ int oracle_find_batch(const oracle_geometry *g, int n_theta, int n_rho,
             return rc;
     }
     return 0;
+}
+
+/* ------------------------------------------------------------ time slicing */
+
+/*
+ * Overlapping time windows (Section 5: the hits are divided into overlapping
+ * windows of 10 ns with a sliding step of 5 ns; Section 6: one window per
+ * unit of work).  Window k, 0 <= k < n_windows, holds every hit h with
+ *     t0 + k*step <= t[h] < t0 + k*step + len,
+ * in input order; a hit lies in every window that covers its time.  The
+ * result is CSR: window k owns index[offsets[k] .. offsets[k+1]), index[j]
+ * being the input position of the hit.  This is the definition written out
+ * as a double loop over windows and hits (no sorting is assumed here).
+ * Returns the number of entries, -1 on bad arguments, -2 when they would
+ * not fit in `capacity`.
+ */
+int64_t oracle_time_slice(const int64_t *t, int64_t n, int64_t t0, int64_t step, int64_t len,
+                          int64_t n_windows, int64_t *offsets, int64_t *index, int64_t capacity)
+{
+    if (n < 0 || step <= 0 || len <= 0 || n_windows < 0 || (n > 0 && !t) || !offsets)
+        return -1;
+    int64_t m = 0;
+    for (int64_t k = 0; k < n_windows; ++k) {
+        const int64_t start = t0 + k * step;
+        const int64_t end = start + len;
+        offsets[k] = m;
+        for (int64_t h = 0; h < n; ++h) {
+            if (t[h] >= start && t[h] < end) {
+                if (m >= capacity)
+                    return -2;
+                index[m] = h;
+                ++m;
+            }
+        }
+    }
+    offsets[n_windows] = m;
+    return m;
 }

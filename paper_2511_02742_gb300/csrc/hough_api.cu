@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -582,6 +583,50 @@ int hough_find_noalloc(const hough_geometry *g, int n_theta, int n_rho,
     if (n_windows == 0)
         return HOUGH_OK;
     return launch_find(&ctx, hits, window_offsets, n_windows, tracks_out, s, counter, l);
+}
+
+int hough_time_slice(hough_ctx *ctx, const int64_t *t, const int32_t *in0, const int32_t *in1,
+                     int64_t n_hits, int64_t t0, int64_t step, int64_t len, int64_t n_windows,
+                     int32_t *out0, int32_t *out1, int64_t *out_index, int64_t out_capacity,
+                     int64_t *window_offsets, uint32_t *status, void *stream)
+{
+    if (!ctx || n_hits < 0 || n_windows < 0 || step <= 0 || len <= 0 || !window_offsets ||
+        (n_hits > 0 && (!t || !in0 || !in1 || !out0 || !out1)))
+        return fail(ctx, HOUGH_ERR_INVALID_ARG);
+    if (len % step != 0 || len / step > HOUGH_SLICE_MAX_OVERLAP)
+        return fail(ctx, HOUGH_ERR_UNSUPPORTED_SHAPE);
+    const int m = (int)(len / step);
+    if (out_capacity < 0 || (n_hits > 0 && out_capacity / m < n_hits))
+        return fail(ctx, HOUGH_ERR_INVALID_ARG);
+    // the window starts must stay inside int64
+    const long long lim = (long long)(INT64_MAX / 4);
+    if (t0 > lim || t0 < -lim || step > lim / (n_windows + m + 1))
+        return fail(ctx, HOUGH_ERR_INVALID_ARG);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (status && cudaMemsetAsync(status, 0, sizeof(uint32_t), s) != cudaSuccess)
+        return fail(ctx, HOUGH_ERR_CUDA);
+    hk::SliceParams q{};
+    q.t = reinterpret_cast<const long long *>(t);
+    q.in0 = in0;
+    q.in1 = in1;
+    q.n = n_hits;
+    q.t0 = t0;
+    q.step = step;
+    q.n_windows = n_windows;
+    q.cap = out_capacity;
+    q.m = m;
+    q.out0 = out0;
+    q.out1 = out1;
+    q.out_index = reinterpret_cast<long long *>(out_index);
+    q.offsets = reinterpret_cast<long long *>(window_offsets);
+    q.status = status;
+    const long long warps_needed = n_windows + 1;
+    const long long blocks = std::min<long long>((warps_needed + 7) / 8, (long long)ctx->num_sms * 8);
+    hk::slice_kernel<<<(unsigned)std::max<long long>(blocks, 1), 256, 0, s>>>(q);
+    if (cudaGetLastError() != cudaSuccess)
+        return fail(ctx, HOUGH_ERR_CUDA);
+    ctx->launches += 1;
+    return HOUGH_OK;
 }
 
 int hough_find_host(hough_ctx *ctx, const hough_hits *hits, const int64_t *window_offsets,

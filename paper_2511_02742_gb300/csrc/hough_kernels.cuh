@@ -281,21 +281,34 @@ __device__ void vote_tile(const KParams &p, uint32_t *acc, const int2 *stage, in
     const unsigned nr = (unsigned)p.n_rho;
     const unsigned tm1 = (unsigned)(p.T - 1);
     bool oor = false;
+    // Software pipelined: the next hit is loaded before this hit's atomics
+    // (which the "memory" clobber keeps in program order), and all P atomics
+    // are issued before any returned value is tested.
+    int h = warp / G;
+    int2 nxt = stage[max(min(h, nh - 1), 0)];
 #pragma unroll 2
-    for (int h = warp / G; h < nh; h += hstep) {
-        const int2 hv = stage[h];
+    for (; h < nh; h += hstep) {
+        const int2 hv = nxt;
+        nxt = stage[min(h + hstep, nh - 1)];
+        int bb[P];
+        bool in[P];
+        unsigned old[P];
 #pragma unroll
         for (int k = 0; k < P; ++k) {
-            const int b = rho_bin(hv.x, hv.y, c[k], s[k], D, K);
-            bool in = true;
+            bb[k] = rho_bin(hv.x, hv.y, c[k], s[k], D, K);
+            in[k] = true;
             if (!FAST) {
-                in = act[k] && (unsigned)b < nr;
-                oor |= act[k] && !in;
+                in[k] = act[k] && (unsigned)bb[k] < nr;
+                oor |= act[k] && !in[k];
             }
-            const unsigned old = in ? atom_add_shared(col + (unsigned)b * 128u, 1u << (k * CW)) : 0u;
-            if (in && ((old >> (k * CW)) & MASK) == tm1)
-                list_append(seg, L, cnt, ovf, ((col_word0 + (unsigned)b * 32u) << 2) | (unsigned)k);
         }
+#pragma unroll
+        for (int k = 0; k < P; ++k)
+            old[k] = in[k] ? atom_add_shared(col + (unsigned)bb[k] * 128u, 1u << (k * CW)) : 0u;
+#pragma unroll
+        for (int k = 0; k < P; ++k)
+            if (in[k] && ((old[k] >> (k * CW)) & MASK) == tm1)
+                list_append(seg, L, cnt, ovf, ((col_word0 + (unsigned)bb[k] * 32u) << 2) | (unsigned)k);
     }
     if (oor)
         atomicOr(&ws.flags, HOUGH_WIN_VOTE_OUT_OF_RANGE);
@@ -842,15 +855,15 @@ __device__ int process_tiles(const KParams &p, long long beg, int H, uint32_t *a
         const int ihi = rhi - t0;
         list_carry<P>(p, tv, rlo, rhi, my_cl, L, cnt, ovf);
         __syncthreads();
-        // block-wide exclusive prefix of the lanes' counts; lane 31 also owns
-        // its warp's overflow entries (only an overflow area past its
-        // capacity sends the tile to the direct test)
-        int my_n = 0, my_pre = 0;   // this thread's entries and their first index
+        // block-wide exclusive prefix: a warp's entries are its lanes' column
+        // entries in lane order, then its overflow entries (only an overflow
+        // area past its capacity sends the tile to the direct test)
+        int my_pre = 0;             // index of this lane's first column entry
+        int ovf_pre = 0, n_ovf_w = 0;   // index and number of the warp's overflow entries
         {
             const int n_ovf = wc.n_ovf[warp];
-            int c = cnt;
-            if (lane == 31)
-                c += min(n_ovf, p.seg_ovf);
+            n_ovf_w = min(n_ovf, p.seg_ovf);
+            const int c = cnt;
             int incl = c;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
@@ -859,7 +872,7 @@ __device__ int process_tiles(const KParams &p, long long beg, int H, uint32_t *a
                     incl += y;
             }
             if (lane == 31)
-                wc.n_cl[warp] = incl;
+                wc.n_cl[warp] = incl + n_ovf_w;
             const bool lost = __syncthreads_or(lane == 0 && n_ovf > p.seg_ovf);
             if (warp == 0) {
                 const int wt = lane < nw ? wc.n_cl[lane] : 0;
@@ -878,8 +891,8 @@ __device__ int process_tiles(const KParams &p, long long beg, int H, uint32_t *a
                 }
             }
             __syncthreads();
-            my_n = c;
             my_pre = wc.pre_cl[warp] + incl - c;
+            ovf_pre = wc.pre_cl[warp] + __shfl_sync(0xffffffffu, incl, 31);
         }
         PeakSink ps{keys + p.kp + (size_t)warp * seg_cap, seg_cap, wc.n_pk[warp], 0, ws.kth,
                     ws.vk, vh + warp * kHistBins};
@@ -896,14 +909,16 @@ __device__ int process_tiles(const KParams &p, long long beg, int H, uint32_t *a
             const int B = blockDim.x, lnw = __ffs(nw) - 1;
             for (int base = 0; base < total; base += p.cmp_cap) {
                 const int hi = min(total - base, p.cmp_cap);
-                for (int j = 0; j < my_n; ++j) {
-                    const int y = my_pre + j - base;
+                auto put = [&](int y, uint32_t e) {
                     if (y >= 0 && y < hi) {
-                        const uint32_t e = j < cnt ? my_cl[j * 32 + lane] : my_cl[L * 32 + (j - cnt)];
                         const int yl = y & (B - 1);
                         cmp[(y - yl) + ((yl & (nw - 1)) << 5) + (yl >> lnw)] = e;
                     }
-                }
+                };
+                for (int j = 0; j < cnt; ++j)
+                    put(my_pre + j - base, my_cl[j * 32 + lane]);
+                for (int j = lane; j < n_ovf_w; j += 32)          // the whole warp
+                    put(ovf_pre + j - base, my_cl[L * 32 + j]);
                 __syncthreads();
                 for (int c0 = 0; c0 < hi; c0 += B) {
                     const int y = c0 + (lane << lnw) + warp;
@@ -1210,6 +1225,87 @@ __global__ void encode_kernel(const int32_t *vane, const int32_t *strip, long lo
         phi_q[i] = (int32_t)((long long)vane_step * (long long)__ldg(vane + i));
         z_q[i] = (int32_t)((long long)z_min_u + (long long)z_pitch_u * (long long)__ldg(strip + i) +
                            z_half);
+    }
+}
+
+
+// ------------------------------------------------------------ time slicing
+//
+// Window k holds the hits with t0 + k*step <= t < t0 + (k + m)*step (window
+// length m steps).  With LB(j) = the first hit whose time is >= t0 + j*step
+// (a lower bound on the sorted times), window k is hits [LB(k), LB(k + m))
+// and, the counts telescoping, its first output place is
+//     offsets[k] = sum_{i<m} LB(k + i) - sum_{i<m} LB(i),
+// so every window finds its place from m + 1 binary searches, without a scan
+// over the windows.  One warp per window: lanes 0..m run the searches, then
+// the warp copies the window's hits (coalesced, contiguous on both sides).
+struct SliceParams {
+    const long long *t;
+    const int32_t *in0, *in1;
+    long long n, t0, step, n_windows, cap;
+    int m;
+    int32_t *out0, *out1;
+    long long *out_index;
+    long long *offsets;
+    unsigned int *status;
+};
+
+__device__ __forceinline__ long long lower_bound_time(const long long *t, long long n, long long v)
+{
+    long long lo = 0, hi = n;
+    while (lo < hi) {
+        const long long mid = lo + ((hi - lo) >> 1);
+        if (__ldg(t + mid) < v)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) slice_kernel(SliceParams q)
+{
+    const int lane = threadIdx.x & 31;
+    const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long n_warps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const unsigned full = 0xffffffffu;
+    // sortedness, every adjacent pair once over the grid
+    bool bad = false;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i + 1 < q.n;
+         i += (long long)gridDim.x * blockDim.x)
+        bad |= __ldg(q.t + i) > __ldg(q.t + i + 1);
+    if (__any_sync(full, bad) && lane == 0 && q.status)
+        atomicOr(q.status, HOUGH_SLICE_UNSORTED);
+    // sum_{i<m} LB(i)
+    long long lb0 = lane < q.m ? lower_bound_time(q.t, q.n, q.t0 + (long long)lane * q.step) : 0;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1)
+        lb0 += __shfl_xor_sync(full, lb0, d);
+    const long long base = lb0;
+    for (long long k = gwarp; k <= q.n_windows; k += n_warps) {
+        const long long lb = lane <= q.m
+                                 ? lower_bound_time(q.t, q.n, q.t0 + (k + lane) * q.step)
+                                 : 0;
+        long long s = lane < q.m ? lb : 0;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1)
+            s += __shfl_xor_sync(full, s, d);
+        const long long off = s - base;
+        if (lane == 0)
+            q.offsets[k] = off;
+        if (k == q.n_windows)
+            break;                                   // offsets[n_windows] only
+        const long long lo = __shfl_sync(full, lb, 0);
+        const long long hi = __shfl_sync(full, lb, q.m);
+        // unsorted input can give any lo, hi and off: copy only what fits
+        if (lo < hi && off >= 0 && off + (hi - lo) <= q.cap) {
+            for (long long j = lane; j < hi - lo; j += 32) {
+                q.out0[off + j] = __ldg(q.in0 + lo + j);
+                q.out1[off + j] = __ldg(q.in1 + lo + j);
+                if (q.out_index)
+                    q.out_index[off + j] = lo + j;
+            }
+        }
     }
 }
 

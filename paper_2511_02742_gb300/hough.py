@@ -30,6 +30,8 @@ HOUGH_FLAG_EXPORT_ACC = 1
 HOUGH_ERR_TIMEOUT = -4
 HOUGH_ERR_UNSUPPORTED_SHAPE = -5
 HOUGH_ERR_BUSY = -7
+HOUGH_SLICE_MAX_OVERLAP = 16
+HOUGH_SLICE_UNSORTED = 1
 
 PEAK_DTYPE = np.dtype([("theta", "<u2"), ("rho", "<u2"), ("votes", "<i4"),
                        ("n_hits", "<i4"), ("hit_begin", "<i4")])
@@ -138,6 +140,7 @@ def load(build_if_missing: bool = False):
         "hough_status_string": ([i32], ctypes.c_char_p),
         "hough_last_error": ([P], i32),
         "hough_launch_count": ([P], i64),
+        "hough_time_slice": ([P, P, P, P, i64, i64, i64, i64, i64, P, P, P, i64, P, P, P], i32),
         "hough_server_create": ([P, P, P], i32),
         "hough_server_submit": ([P, P, P], i32),
         "hough_server_wait": ([P, ctypes.c_uint64, i64, P], i32),
@@ -236,6 +239,17 @@ def make_tracks(out: dict) -> hough_tracks:
 def hough_encode(ctx, vane, strip, phi_q, z_q, stream=None) -> None:
     _check(load().hough_encode(ctx, _ptr(vane), _ptr(strip), len(vane), _ptr(phi_q), _ptr(z_q),
                                _stream(stream)), "hough_encode")
+
+
+def hough_time_slice(ctx, t, in0, in1, t0: int, step: int, length: int, n_windows: int,
+                     out0, out1, out_index, window_offsets, status=None, stream=None) -> None:
+    """Overlapping time windows on the device (device tensors; see hough.h)."""
+    n = int(t.numel())
+    cap = int(out0.numel())
+    _check(load().hough_time_slice(ctx, _ptr(t), _ptr(in0), _ptr(in1), n, int(t0), int(step),
+                                   int(length), int(n_windows), _ptr(out0), _ptr(out1),
+                                   _ptr(out_index), cap, _ptr(window_offsets), _ptr(status),
+                                   _stream(stream)), "hough_time_slice")
 
 
 def hough_find(ctx, hits: hough_hits, window_offsets, n_windows: int, tracks_out: hough_tracks,
@@ -388,6 +402,27 @@ class Finder:
         n_windows = int(offsets.numel()) - 1
         return hough_plan_create(self.ctx, self.hits_struct(hits), offsets, n_windows,
                                  make_tracks(out), stream)
+
+    def time_slice(self, t, hits: dict, t0: int, step: int, length: int, n_windows: int,
+                   stream=None) -> dict:
+        """Cut a time-ordered hit stream (device tensors) into overlapping
+        windows; returns dict(hits=..., offsets, index, status, capacity) ready
+        for find()."""
+        import torch
+        n = int(t.numel())
+        cap = max(1, n * (length // step))
+        raw = "vane" in hits
+        a, b = (hits["vane"], hits["strip"]) if raw else (hits["phi_q"], hits["z_q"])
+        dev = t.device
+        o0 = torch.empty(cap, dtype=torch.int32, device=dev)
+        o1 = torch.empty(cap, dtype=torch.int32, device=dev)
+        idx = torch.empty(cap, dtype=torch.int64, device=dev)
+        offs = torch.empty(n_windows + 1, dtype=torch.int64, device=dev)
+        status = torch.empty(1, dtype=torch.int32, device=dev)
+        hough_time_slice(self.ctx, t, a, b, t0, step, length, n_windows, o0, o1, idx, offs,
+                         status, stream)
+        sliced = dict(vane=o0, strip=o1) if raw else dict(phi_q=o0, z_q=o1)
+        return dict(hits=sliced, offsets=offs, index=idx, status=status, capacity=cap)
 
     def autotune(self, hits: dict, offsets, out: dict, iters=3, stream=None) -> dict:
         n_windows = int(offsets.numel()) - 1

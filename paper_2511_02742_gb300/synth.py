@@ -229,6 +229,42 @@ def generate(n_windows: int, tracks, p_range=(100.0, 300.0), noise_frac=0.0, see
                    z_h[order].copy(), params, track_off)
 
 
+@dataclass
+class TimedHits:
+    """A time-ordered hit stream (Section 5 time slicing): t in picoseconds."""
+    t: np.ndarray          # int64 [n], non-decreasing
+    vane: np.ndarray       # int32 [n]
+    strip: np.ndarray      # int32 [n]
+    track: np.ndarray      # int64 [n]: generating track, -1 for noise
+
+    @property
+    def n_hits(self) -> int:
+        return len(self.t)
+
+
+def timed_stream(duration_ns: float, rate_per_ns: float, p_range=(100.0, 300.0),
+                 noise_frac=0.0, seed=0, spread_ps=2000) -> TimedHits:
+    """Decays as a Poisson process of `rate_per_ns` over `duration_ns` (the
+    paper's pileup rates are 0.06, 0.6 and 6 decays per ns); each track's
+    hits arrive within `spread_ps` of its decay time; noise hits are spread
+    uniformly over the stream.  Hits are sorted by time (stable)."""
+    rng = np.random.default_rng(seed)
+    dur_ps = int(round(duration_ns * 1000))
+    n_tracks = int(rng.poisson(rate_per_ns * duration_ns))
+    w = generate(n_tracks, 1, p_range, 0.0, seed=int(rng.integers(1 << 31)), shuffle=False)
+    t_dec = rng.integers(0, max(dur_ps, 1), n_tracks)
+    trk = np.repeat(np.arange(n_tracks, dtype=np.int64), np.diff(w.offsets))
+    t_sig = t_dec[trk] + rng.integers(0, spread_ps, len(trk))
+    n_noise = int(round(noise_frac * len(trk)))
+    t_noise = rng.integers(0, max(dur_ps, 1) + spread_ps, n_noise)
+    t = np.concatenate([t_sig, t_noise]).astype(np.int64)
+    vane = np.concatenate([w.vane, rng.integers(0, N_VANES, n_noise).astype(np.int32)])
+    strip = np.concatenate([w.strip, rng.integers(0, N_Z_STRIPS, n_noise).astype(np.int32)])
+    track = np.concatenate([trk, np.full(n_noise, -1, np.int64)])
+    order = np.argsort(t, kind="stable")
+    return TimedHits(t[order].copy(), vane[order].copy(), strip[order].copy(), track[order].copy())
+
+
 def line_window(theta_deg: float, rho: float, vanes=None) -> Windows:
     """One window whose hits lie on the straight line phi*cos(theta) + z*sin(theta) = rho
     (phi in degrees at each vane, z in mm), digitised to strips; vanes whose

@@ -8,6 +8,14 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
+@pytest.fixture(scope="module")
+def hough():
+    """The binding of the CUDA library, loaded (fails if it is not built)."""
+    from paper_2511_02742_gb300 import hough as h
+    h.load()
+    return h
+
+
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (runs the CUDA library)")
     config.addinivalue_line("markers", "slow: long-running case")

@@ -14,13 +14,6 @@ from parity_helpers import G, assert_batch_equal, assert_window_equal, gpu_run, 
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def hough():
-    from paper_2511_02742_gb300 import hough as h
-    h.load()
-    return h
-
-
 def _finder(hough, n_theta, n_rho, **kw):
     return hough.Finder(n_theta, n_rho, **kw)
 
