@@ -149,6 +149,49 @@ def _cpu_baseline(w, n_theta, n_rho, budget_s=12.0):
             "sample_single_core": f"first {n1} windows, 1 thread ({dt1:.1f} s)"}
 
 
+def _coarse_fine_leg(args, dev, stream, flush, w, hits, offs):
+    """The paper's own two-stage search (coarse 18 x 100, then 10 x 10 of the
+    180 x 1000 grid; one line per window) on the same batch, and how often its
+    line is the top peak of the full 180 x 1000 search of this library."""
+    import torch
+    from paper_2511_02742_gb300 import hough
+    f = hough.Finder(180, 1000)
+    lines = torch.empty((w.n_windows, 8), dtype=torch.int32, device=dev)
+    ht = torch.empty(max(w.n_hits, 1), dtype=torch.int32, device=dev)
+    hs = f.hits_struct(hits)
+    for _ in range(3):
+        hough.hough_find_coarse_fine(f.ctx, hs, offs, w.n_windows, lines, ht, stream)
+    torch.cuda.synchronize()
+    steps = max(1, min(args.steps, 10))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for i in range(steps):
+        _flush_l2(flush)
+        ev[i][0].record(stream)
+        hough.hough_find_coarse_fine(f.ctx, hs, offs, w.n_windows, lines, ht, stream)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    # agreement with the full-resolution top peak on the paper's grid
+    n_cmp = min(w.n_windows, 20000)
+    full = f.find(hits, offs[:n_cmp + 1], stream=stream)
+    torch.cuda.synchronize()
+    lv = lines.cpu().numpy()[:n_cmp].view(hough.LINE_DTYPE).reshape(-1)
+    pk = hough.decode_peaks(full["peaks"])
+    npk = full["n_peaks"].cpu().numpy()
+    both = (lv["found"] == 1) & (npk > 0)
+    tt = np.array([pk[k][0]["theta"] if npk[k] > 0 else -9 for k in range(n_cmp)])
+    rr = np.array([pk[k][0]["rho"] if npk[k] > 0 else -9 for k in range(n_cmp)])
+    same = both & (tt == lv["fine_theta"]) & (rr == lv["fine_rho"])
+    near = both & (np.abs(tt - lv["fine_theta"]) <= 1) & (np.abs(rr - lv["fine_rho"]) <= 1)
+    f.close()
+    return {"method": "coarse 18x100 then fine 10x10 of the 180x1000 grid, one line per window",
+            "ms_per_step": round(ms, 4), "windows_per_s": round(w.n_windows / (ms * 1e-3), 1),
+            "windows_with_line": int((lv["found"] == 1).sum()), "compared_windows": n_cmp,
+            "same_bin_as_full_top_peak": round(float(same.sum()) / max(int(both.sum()), 1), 4),
+            "within_one_bin": round(float(near.sum()) / max(int(both.sum()), 1), 4)}
+
+
 def _slicing_leg(args, dev, stream, flush, hbm_gbs):
     """Time slicing on the device (Section 5: 10 ns windows sliding by 5 ns)
     of a time-ordered stream, then the whole find over the sliced windows.
@@ -237,15 +280,20 @@ def _serving_leg(args, dev):
     dt_ns = int(args.serve_slice_ms * 1e6)
     n_slices = int(round(args.serve_seconds * 1e3 / args.serve_slice_ms))
     counts = np.random.default_rng(11).poisson(args.serve_rate * dt_ns * 1e-9, n_slices)
+    if args.serve_launch:
+        hough.hough_set_launch(f.ctx, *[int(x) for x in args.serve_launch.split(",")])
+    launch_used = hough.hough_get_launch(f.ctx)
     srv = hough.Server(f, n_slots=4, slot_windows=4096, slot_hits=1 << 21, max_queued=1 << 16)
     clock = hough.hough_server_clock_ns
-    ranges, lat, bsz, bwin = {}, [], [], []
+    ranges, lat, bsz, bwin, wait, gpu = {}, [], [], [], [], []
     state = {"mism": 0, "done": 0, "last_done": 0}
 
     def handle(rs):
         for r in rs:
             a, b = ranges.pop(r["ticket"])
             lat.append((r["done_ns"] - r["arrival_ns"]) * 1e-3)
+            wait.append((r["launch_ns"] - r["arrival_ns"]) * 1e-3)
+            gpu.append((r["done_ns"] - r["launch_ns"]) * 1e-3)
             bsz.append(r["batch_requests"])
             bwin.append(r["batch_windows"])
             state["last_done"] = max(state["last_done"], r["done_ns"])
@@ -305,6 +353,9 @@ def _serving_leg(args, dev):
             "p99_us": round(float(np.percentile(lat_a, 99)), 1),
             "p999_us": round(float(np.percentile(lat_a, 99.9)), 1),
             "max_us": round(float(lat_a.max()), 1),
+            "p50_queue_us": round(float(np.percentile(wait, 50)), 1),
+            "p50_launch_to_done_us": round(float(np.percentile(gpu, 50)), 1),
+            "launch": launch_used,
             "mean_batch_requests": round(float(np.mean(bsz)), 2),
             "mean_batch_windows": round(float(np.mean(bwin)), 1),
             "batches": st["batches"], "late_submits": late,
@@ -559,6 +610,8 @@ def run_ours(args):
         serving = _serving_leg(args, dev) if args.serve_seconds > 0 else None
         slicing = _slicing_leg(args, dev, stream, flush, peaks_meas.get("hbm_gbs")) \
             if args.slice_us > 0 else None
+        coarse_fine = _coarse_fine_leg(args, dev, stream, flush, w, hits, offs) \
+            if args.coarse_fine else None
         result = {
             "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
@@ -587,6 +640,7 @@ def run_ours(args):
             "roofline_export": export,
             "serving": serving,
             "time_slicing": slicing,
+            "coarse_to_fine": coarse_fine,
             "latency_us": {"p50": serving["p50_us"], "p99": serving["p99_us"],
                            "source": "serving leg"} if serving else None,
             "cpu_baseline": cpu,
@@ -641,7 +695,10 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=1e5)
     ap.add_argument("--serve-slice-ms", type=float, default=1.0)
     ap.add_argument("--serve-pool", type=int, default=20000)
+    ap.add_argument("--serve-launch", default="",
+                    help="threads,word_rows,hit_stage,ctas_per_sm for the serving context")
     ap.add_argument("--slice-us", type=float, default=100.0)
+    ap.add_argument("--no-coarse-fine", dest="coarse_fine", action="store_false")
     ap.add_argument("--slice-rate", type=float, default=0.6)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the library's default launch shape instead of autotuning it")

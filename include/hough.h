@@ -214,6 +214,40 @@ int hough_find(hough_ctx *ctx, const hough_hits *hits, const int64_t *window_off
                int64_t n_windows, const hough_tracks *tracks_out, void *stream);
 
 /*
+ * The paper's own two-stage GPU search, one line per window (Section 6 and
+ * its figure of the Hough steps: a coarse histogram of 18 theta x 100 rho
+ * bins, then a 10 x 10 fine histogram around its high-likelihood zone, the
+ * fine maximum giving the line; seeds are the hits on that line).  Reading:
+ * coarse bins of 10 degrees x 10 rho units over the same ranges as the full
+ * histogram; the coarse bin with the most entries (ties: first in row-major
+ * order); the fine histogram is the 10 x 10 block of the paper's 180 x 1000
+ * grid (Section 5: 1 degree x 1 unit) inside that coarse bin: fine row
+ * 10*coarse_theta + i, fine rho bin 10*coarse_rho + j; its highest bin (ties
+ * row-major) is the line, kept if both maxima reach vote_threshold.  Seeds:
+ * the valid hits whose bin in the line's fine row is within assoc_tol_bins
+ * of the line's bin.  Same fixed-point arithmetic as hough_find, with the
+ * 18 x 100 and 180 x 1000 tables of hough_tables.
+ *   lines[n_windows]     device, one result per window;
+ *   hit_track[n_hits]    device, 0 for a seed, -1 for a hit off the line (or
+ *                        a window without one), -2 outside the detector box.
+ * Hits and offsets as hough_find.  Asynchronous on stream.
+ * Errors: INVALID_ARG, CUDA.
+ */
+typedef struct hough_line {
+    int32_t coarse_theta;   /* 0..17   */
+    int32_t coarse_rho;     /* 0..99   */
+    int32_t coarse_votes;
+    int32_t fine_theta;     /* 0..179, row of the 180 x 1000 grid */
+    int32_t fine_rho;       /* 0..999  */
+    int32_t fine_votes;
+    int32_t n_seeds;
+    int32_t found;          /* 1 if the window has a line */
+} hough_line;
+int hough_find_coarse_fine(hough_ctx *ctx, const hough_hits *hits, const int64_t *window_offsets,
+                           int64_t n_windows, hough_line *lines, int32_t *hit_track,
+                           void *stream);
+
+/*
  * Time slicing on the device (Section 5: the hits of a readout are divided
  * into overlapping time windows of 10 ns with a sliding step of 5 ns;
  * Section 6: each window is one unit of work).  Window k, 0 <= k < n_windows,
@@ -345,6 +379,9 @@ typedef struct hough_server_config {
     int64_t slot_windows;  /* windows one batch can hold (>= 1)                         */
     int64_t slot_hits;     /* hits one batch can hold (>= 1)                            */
     int64_t max_queued;    /* requests waiting for a slot before submit says BUSY (>= 1) */
+    hough_launch launch;   /* launch shape of the server's batches; all 0: one CTA per
+                              SM with the largest tile (the lowest latency for small
+                              batches), restored on the context by hough_server_destroy */
 } hough_server_config;
 
 /*

@@ -27,6 +27,10 @@ _lib = None
 PEAK_DTYPE = np.dtype([("theta", "<u2"), ("rho", "<u2"), ("votes", "<i4"),
                        ("n_hits", "<i4"), ("hit_begin", "<i4")])
 
+CF_DTYPE = np.dtype([(k, "<i4") for k in ("coarse_theta", "coarse_rho", "coarse_votes",
+                                            "fine_theta", "fine_rho", "fine_votes", "n_seeds",
+                                            "found")])
+
 WIN_PEAK_OVERFLOW = 1
 WIN_HIT_OUT_OF_RANGE = 2
 WIN_VOTE_OUT_OF_RANGE = 4
@@ -81,6 +85,10 @@ def _load():
         lib.oracle_find_batch.restype = i32
         lib.oracle_time_slice.argtypes = [P, i64, i64, i64, i64, i64, P, P, i64]
         lib.oracle_time_slice.restype = i64
+        lib.oracle_coarse_fine_window.argtypes = [P, P, P, P, i64, P, P]
+        lib.oracle_coarse_fine_window.restype = i32
+        lib.oracle_coarse_fine_batch.argtypes = [P, P, P, P, P, i64, P, P]
+        lib.oracle_coarse_fine_batch.restype = i32
         _lib = lib
     return _lib
 
@@ -239,3 +247,22 @@ def time_slice(t, t0: int, step: int, length: int, n_windows: int):
     if m < 0:
         raise ValueError(f"oracle_time_slice: error {m}")
     return offsets, index[:m].copy()
+
+
+def coarse_fine(geom: dict, phi_q, z_q, offsets, vote_threshold=5, assoc_tol_bins=1):
+    """The paper's coarse (18 x 100) then fine (10 x 10 of the 180 x 1000 grid)
+    search, one line per window: (result[n_windows] CF_DTYPE, hit_track)."""
+    lib = _load()
+    g = make_geometry(geom)
+    th = make_thresholds(vote_threshold, assoc_tol_bins, 0)
+    phi_q = np.ascontiguousarray(phi_q, np.int32)
+    z_q = np.ascontiguousarray(z_q, np.int32)
+    offsets = np.ascontiguousarray(offsets, np.int64)
+    nw = len(offsets) - 1
+    out = np.zeros(nw, CF_DTYPE)
+    ht = np.zeros(max(len(phi_q), 1), np.int32)
+    rc = lib.oracle_coarse_fine_batch(ctypes.byref(g), ctypes.byref(th), _ptr(phi_q), _ptr(z_q),
+                                      _ptr(offsets), nw, _ptr(out), _ptr(ht))
+    if rc != 0:
+        raise ValueError("oracle_coarse_fine_batch: bad arguments")
+    return out, ht[:len(phi_q)]

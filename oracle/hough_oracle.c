@@ -487,3 +487,130 @@ int64_t oracle_time_slice(const int64_t *t, int64_t n, int64_t t0, int64_t step,
     offsets[n_windows] = m;
     return m;
 }
+
+/* ------------------------------------------------------ coarse-to-fine search */
+
+/*
+ * The paper's two-stage search for one line per window (Section 6 and the
+ * figure of the Hough steps: a coarse 18 x 100 histogram, then a 10 x 10 fine
+ * histogram around the high-likelihood zone, whose highest bin gives the
+ * line).  Reading: the coarse histogram has 18 theta bins (10 degrees) and
+ * 100 rho bins (10 units) over the same ranges as the full one; the coarse
+ * bin with the most entries is taken (ties: first in row-major order); the
+ * fine histogram covers that coarse bin with the 1-degree x 1-unit bins of
+ * the paper's 180 x 1000 grid (Section 5): fine row tc*10 + i, fine rho bin
+ * bc*10 + j, 0 <= i, j < 10.  Its highest bin (ties row-major) is the line.
+ * If the coarse or the fine maximum is below T the window has no line.
+ * Seeds: the valid hits whose bin in the line's row is within tol of its bin.
+ */
+typedef struct {
+    int32_t coarse_theta, coarse_rho, coarse_votes;
+    int32_t fine_theta, fine_rho, fine_votes;
+    int32_t n_seeds;
+    int32_t found;
+} oracle_cf;
+
+#define CF_COARSE_THETA 18
+#define CF_COARSE_RHO 100
+#define CF_FINE_THETA 180
+#define CF_FINE_RHO 1000
+#define CF_BLOCK 10
+
+int oracle_coarse_fine_window(const oracle_geometry *g, const oracle_thresholds *th,
+                              const int32_t *phi_q, const int32_t *z_q, int64_t n,
+                              oracle_cf *out, int32_t *hit_track)
+{
+    int32_t Cc[CF_COARSE_THETA], Sc[CF_COARSE_THETA], Cf[CF_FINE_THETA], Sf[CF_FINE_THETA];
+    int64_t Dc = 0, Df = 0;
+    int kc = oracle_tables(g, CF_COARSE_THETA, CF_COARSE_RHO, Cc, Sc, &Dc);
+    int kf = oracle_tables(g, CF_FINE_THETA, CF_FINE_RHO, Cf, Sf, &Df);
+    if (kc < 0 || kf < 0 || !th || !out)
+        return -1;
+    int32_t coarse[CF_COARSE_THETA][CF_COARSE_RHO];
+    int32_t fine[CF_BLOCK][CF_BLOCK];
+    memset(coarse, 0, sizeof(coarse));
+    memset(fine, 0, sizeof(fine));
+    memset(out, 0, sizeof(*out));
+    /* coarse histogram over every valid hit */
+    for (int64_t h = 0; h < n; ++h) {
+        if (!hit_is_valid(g, phi_q[h], z_q[h]))
+            continue;
+        for (int t = 0; t < CF_COARSE_THETA; ++t) {
+            int64_t b = rho_bin(phi_q[h], z_q[h], Cc[t], Sc[t], Dc, kc);
+            if (b >= 0 && b < CF_COARSE_RHO)
+                coarse[t][b] += 1;
+        }
+    }
+    int tc = 0, bc = 0;
+    for (int t = 0; t < CF_COARSE_THETA; ++t)
+        for (int b = 0; b < CF_COARSE_RHO; ++b)
+            if (coarse[t][b] > coarse[tc][bc]) {
+                tc = t;
+                bc = b;
+            }
+    out->coarse_theta = tc;
+    out->coarse_rho = bc;
+    out->coarse_votes = coarse[tc][bc];
+    int found = out->coarse_votes >= th->vote_threshold;
+    int tf = 0, bf = 0;
+    if (found) {
+        /* fine histogram: the 10 x 10 bins of the 180 x 1000 grid inside the
+           coarse bin */
+        for (int64_t h = 0; h < n; ++h) {
+            if (!hit_is_valid(g, phi_q[h], z_q[h]))
+                continue;
+            for (int i = 0; i < CF_BLOCK; ++i) {
+                int t = tc * CF_BLOCK + i;
+                int64_t b = rho_bin(phi_q[h], z_q[h], Cf[t], Sf[t], Df, kf);
+                int64_t j = b - (int64_t)bc * CF_BLOCK;
+                if (j >= 0 && j < CF_BLOCK)
+                    fine[i][j] += 1;
+            }
+        }
+        int bi = 0, bj = 0;
+        for (int i = 0; i < CF_BLOCK; ++i)
+            for (int j = 0; j < CF_BLOCK; ++j)
+                if (fine[i][j] > fine[bi][bj]) {
+                    bi = i;
+                    bj = j;
+                }
+        tf = tc * CF_BLOCK + bi;
+        bf = bc * CF_BLOCK + bj;
+        out->fine_theta = tf;
+        out->fine_rho = bf;
+        out->fine_votes = fine[bi][bj];
+        found = out->fine_votes >= th->vote_threshold;
+    }
+    out->found = found;
+    for (int64_t h = 0; h < n; ++h) {
+        if (!hit_is_valid(g, phi_q[h], z_q[h])) {
+            hit_track[h] = -2;
+            continue;
+        }
+        hit_track[h] = -1;
+        if (found) {
+            int64_t b = rho_bin(phi_q[h], z_q[h], Cf[tf], Sf[tf], Df, kf);
+            if (b - bf <= th->assoc_tol_bins && bf - b <= th->assoc_tol_bins) {
+                hit_track[h] = 0;
+                out->n_seeds += 1;
+            }
+        }
+    }
+    return 0;
+}
+
+int oracle_coarse_fine_batch(const oracle_geometry *g, const oracle_thresholds *th,
+                             const int32_t *phi_q, const int32_t *z_q, const int64_t *offsets,
+                             int64_t n_windows, oracle_cf *out, int32_t *hit_track)
+{
+    for (int64_t w = 0; w < n_windows; ++w) {
+        int64_t b = offsets[w], e = offsets[w + 1];
+        if (b < 0 || e < b)
+            return -1;
+        int rc = oracle_coarse_fine_window(g, th, phi_q + b, z_q + b, e - b, out + w,
+                                           hit_track + b);
+        if (rc != 0)
+            return rc;
+    }
+    return 0;
+}

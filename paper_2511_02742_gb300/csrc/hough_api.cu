@@ -19,6 +19,7 @@
 #include "hough.h"
 #include "hough_internal.h"
 #include "hough_kernels.cuh"
+#include "hough_coarse_fine.cuh"
 
 // Whether every valid hit votes inside [0, n_rho) in every row: the bin is
 // monotone in phi and in z, so the four corners of the detector box bound it.
@@ -443,6 +444,7 @@ void hough_destroy(hough_ctx *ctx)
     cudaFree(ctx->d_C);
     cudaFree(ctx->d_S);
     cudaFree(ctx->stage_dev);
+    cudaFree(ctx->d_cf);
     for (int i = 0; i < 2; ++i) {
         if (ctx->host_streams[i])
             cudaStreamDestroy(ctx->host_streams[i]);
@@ -585,6 +587,79 @@ int hough_find_noalloc(const hough_geometry *g, int n_theta, int n_rho,
     return launch_find(&ctx, hits, window_offsets, n_windows, tracks_out, s, counter, l);
 }
 
+int hough_find_coarse_fine(hough_ctx *ctx, const hough_hits *hits, const int64_t *window_offsets,
+                           int64_t n_windows, hough_line *lines, int32_t *hit_track,
+                           void *stream)
+{
+    if (!ctx || !hits_ok(hits) || n_windows < 0 || (n_windows > 0 && (!window_offsets || !lines)) ||
+        (hits->n_hits > 0 && !hit_track))
+        return fail(ctx, HOUGH_ERR_INVALID_ARG);
+    if (n_windows == 0)
+        return HOUGH_OK;
+    if (!ctx->d_cf) {
+        // the coarse 18 x 100 and fine 180 x 1000 tables, built once
+        std::vector<int32_t> tab(2 * hk::kCfCoarseT + 2 * hk::kCfFineT);
+        int64_t D = 0;
+        int32_t K = 0;
+        int rc = hough_tables(&ctx->g, hk::kCfCoarseT, hk::kCfCoarseR, tab.data(),
+                              tab.data() + hk::kCfCoarseT, &D, &K);
+        if (rc != HOUGH_OK)
+            return fail(ctx, rc);
+        ctx->cf_D[0] = D;
+        ctx->cf_K[0] = K;
+        rc = hough_tables(&ctx->g, hk::kCfFineT, hk::kCfFineR, tab.data() + 2 * hk::kCfCoarseT,
+                          tab.data() + 2 * hk::kCfCoarseT + hk::kCfFineT, &D, &K);
+        if (rc != HOUGH_OK)
+            return fail(ctx, rc);
+        ctx->cf_D[1] = D;
+        ctx->cf_K[1] = K;
+        int32_t *d = nullptr;
+        if (cudaMalloc(&d, sizeof(int32_t) * tab.size()) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, HOUGH_ERR_ALLOC);
+        }
+        if (cudaMemcpy(d, tab.data(), sizeof(int32_t) * tab.size(), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+            cudaFree(d);
+            return fail(ctx, HOUGH_ERR_CUDA);
+        }
+        ctx->d_cf = d;
+    }
+    const hough_geometry &g = ctx->g;
+    const bool raw = hits->vane && hits->strip;
+    hk::CfParams p{};
+    p.a = raw ? hits->vane : hits->phi_q;
+    p.b = raw ? hits->strip : hits->z_q;
+    p.n_hits = hits->n_hits;
+    p.raw = raw ? 1 : 0;
+    p.vane_step = (int)(360LL * g.phi_u_per_deg / g.n_vanes);
+    p.z_min_u = g.z_min_u;
+    p.z_pitch_u = g.z_pitch_u;
+    p.z_half = g.z_pitch_u / 2;
+    p.phi_end = 360LL * g.phi_u_per_deg;
+    p.z_end = (long long)g.z_min_u + (long long)g.n_z_strips * g.z_pitch_u;
+    p.offsets = reinterpret_cast<const long long *>(window_offsets);
+    p.n_windows = n_windows;
+    p.Cc = ctx->d_cf;
+    p.Sc = ctx->d_cf + hk::kCfCoarseT;
+    p.Cf = ctx->d_cf + 2 * hk::kCfCoarseT;
+    p.Sf = ctx->d_cf + 2 * hk::kCfCoarseT + hk::kCfFineT;
+    p.Dc = (int)ctx->cf_D[0];
+    p.Kc = ctx->cf_K[0];
+    p.Df = (int)ctx->cf_D[1];
+    p.Kf = ctx->cf_K[1];
+    p.T = ctx->th.vote_threshold;
+    p.tol = ctx->th.assoc_tol_bins;
+    p.lines = lines;
+    p.hit_track = hit_track;
+    const long long blocks = std::min<long long>(n_windows, (long long)ctx->num_sms * 8);
+    hk::coarse_fine_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(p);
+    if (cudaGetLastError() != cudaSuccess)
+        return fail(ctx, HOUGH_ERR_CUDA);
+    ctx->launches += 1;
+    return HOUGH_OK;
+}
+
 int hough_time_slice(hough_ctx *ctx, const int64_t *t, const int32_t *in0, const int32_t *in1,
                      int64_t n_hits, int64_t t0, int64_t step, int64_t len, int64_t n_windows,
                      int32_t *out0, int32_t *out1, int64_t *out_index, int64_t out_capacity,
@@ -657,6 +732,7 @@ int hough_find_host(hough_ctx *ctx, const hough_hits *hits, const int64_t *windo
     size_t total = al(o_acc + acc_per_w * (size_t)n_windows);
     if (total > ctx->stage_bytes) {
         cudaFree(ctx->stage_dev);
+    cudaFree(ctx->d_cf);
         ctx->stage_dev = nullptr;
         ctx->stage_bytes = 0;
         if (cudaMalloc(&ctx->stage_dev, total) != cudaSuccess) {

@@ -32,4 +32,9 @@ struct hough_ctx {
     size_t stage_bytes = 0;
     cudaStream_t host_streams[2] = {nullptr, nullptr};
     cudaEvent_t host_events[2] = {nullptr, nullptr};
+    // coarse (18 x 100) and fine (180 x 1000) tables of the two-stage search:
+    // C then S of each, on the device; built on first use
+    int32_t *d_cf = nullptr;
+    int cf_K[2] = {0, 0};
+    long long cf_D[2] = {0, 0};
 };

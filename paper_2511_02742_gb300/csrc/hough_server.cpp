@@ -99,6 +99,7 @@ struct Slot {
 struct hough_server {
     hough_ctx *ctx = nullptr;
     hough_server_config cfg{};
+    hough_launch saved_launch{};     // the context's shape before the server
     int max_peaks = 0;
     size_t in_cap = 0, out_cap = 0;
     std::vector<Slot> slots;
@@ -363,6 +364,18 @@ int hough_server_create(hough_ctx *ctx, const hough_server_config *cfg, hough_se
     s->ctx = ctx;
     s->cfg = *cfg;
     s->max_peaks = ctx->th.max_peaks;
+    // the server's launch shape: as given, else one CTA per SM with the
+    // largest tile (small batches then spread over every SM)
+    s->saved_launch = ctx->launch;
+    hough_launch want = cfg->launch;
+    if (want.threads == 0 && want.word_rows == 0 && want.hit_stage == 0 && want.ctas_per_sm == 0)
+        want = hough_launch{512, 0, 2048, 1};
+    if (hough_set_launch(ctx, &want) != HOUGH_OK) {
+        ctx->launch = s->saved_launch;
+        delete s;
+        cudaSetDevice(prev);
+        return HOUGH_ERR_INVALID_ARG;
+    }
     s->in_cap = in_layout(cfg->slot_windows, cfg->slot_hits).total;
     s->out_cap = out_layout(cfg->slot_windows, cfg->slot_hits, s->max_peaks).total;
     s->slots.resize(cfg->n_slots);
@@ -397,6 +410,7 @@ int hough_server_create(hough_ctx *ctx, const hough_server_config *cfg, hough_se
     if (rc != HOUGH_OK) {
         cudaGetLastError();
         free_slots(s);
+        ctx->launch = s->saved_launch;
         delete s;
         cudaSetDevice(prev);
         return rc;
@@ -406,6 +420,7 @@ int hough_server_create(hough_ctx *ctx, const hough_server_config *cfg, hough_se
         s->worker = std::thread(worker_loop, s);
     } catch (...) {
         free_slots(s);
+        ctx->launch = s->saved_launch;
         delete s;
         cudaSetDevice(prev);
         return HOUGH_ERR_ALLOC;
@@ -534,6 +549,7 @@ void hough_server_destroy(hough_server *s)
     cudaGetDevice(&prev);
     cudaSetDevice(s->ctx->device);
     free_slots(s);
+    s->ctx->launch = s->saved_launch;
     cudaSetDevice(prev);
     delete s;
 }

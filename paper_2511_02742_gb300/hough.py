@@ -71,7 +71,7 @@ class hough_launch(ctypes.Structure):
 class hough_server_config(ctypes.Structure):
     _fields_ = [("n_slots", ctypes.c_int32), ("raw_hits", ctypes.c_int32),
                 ("slot_windows", ctypes.c_int64), ("slot_hits", ctypes.c_int64),
-                ("max_queued", ctypes.c_int64)]
+                ("max_queued", ctypes.c_int64), ("launch", hough_launch)]
 
 
 class hough_request(ctypes.Structure):
@@ -140,6 +140,7 @@ def load(build_if_missing: bool = False):
         "hough_status_string": ([i32], ctypes.c_char_p),
         "hough_last_error": ([P], i32),
         "hough_launch_count": ([P], i64),
+        "hough_find_coarse_fine": ([P, P, P, i64, P, P, P], i32),
         "hough_time_slice": ([P, P, P, P, i64, i64, i64, i64, i64, P, P, P, i64, P, P, P], i32),
         "hough_server_create": ([P, P, P], i32),
         "hough_server_submit": ([P, P, P], i32),
@@ -239,6 +240,20 @@ def make_tracks(out: dict) -> hough_tracks:
 def hough_encode(ctx, vane, strip, phi_q, z_q, stream=None) -> None:
     _check(load().hough_encode(ctx, _ptr(vane), _ptr(strip), len(vane), _ptr(phi_q), _ptr(z_q),
                                _stream(stream)), "hough_encode")
+
+
+LINE_DTYPE = np.dtype([(k, "<i4") for k in ("coarse_theta", "coarse_rho", "coarse_votes",
+                                              "fine_theta", "fine_rho", "fine_votes", "n_seeds",
+                                              "found")])
+
+
+def hough_find_coarse_fine(ctx, hits: hough_hits, window_offsets, n_windows: int, lines,
+                           hit_track, stream=None) -> None:
+    """The paper's coarse (18 x 100) then fine (10 x 10) search, one line per
+    window; lines: int32 tensor [n_windows, 8] (hough_line)."""
+    _check(load().hough_find_coarse_fine(ctx, ctypes.byref(hits), _ptr(window_offsets), n_windows,
+                                         _ptr(lines), _ptr(hit_track), _stream(stream)),
+           "hough_find_coarse_fine")
 
 
 def hough_time_slice(ctx, t, in0, in1, t0: int, step: int, length: int, n_windows: int,
@@ -446,12 +461,12 @@ class Server:
     """
 
     def __init__(self, finder: "Finder", n_slots=4, slot_windows=4096, slot_hits=1 << 20,
-                 max_queued=4096, raw_hits=True):
+                 max_queued=4096, raw_hits=True, launch=None):
         self.lib = load()
         self.finder = finder
         self.max_peaks = finder.max_peaks
         cfg = hough_server_config(n_slots, 1 if raw_hits else 0, slot_windows, slot_hits,
-                                  max_queued)
+                                  max_queued, hough_launch(*(launch or (0, 0, 0, 0))))
         h = ctypes.c_void_p()
         _check(self.lib.hough_server_create(finder.ctx, ctypes.byref(cfg), ctypes.byref(h)),
                "hough_server_create")
