@@ -149,6 +149,46 @@ def _cpu_baseline(w, n_theta, n_rho, budget_s=12.0):
             "sample_single_core": f"first {n1} windows, 1 thread ({dt1:.1f} s)"}
 
 
+def _iterative_leg(args, dev, stream, w, hits, offs, out_find):
+    """The iterative highest-bin search on the first --iter-windows windows of
+    the batch, and how many of its tracks are peaks of the local-maximum
+    search (same bin)."""
+    import torch
+    from paper_2511_02742_gb300 import hough, synth
+    cfg = synth.WORKLOADS[args.workload]
+    n = min(w.n_windows, args.iter_windows)
+    f = hough.Finder(cfg["n_theta"], cfg["n_rho"])
+    mt = 64
+    tr = torch.empty((n, mt, 4), dtype=torch.int32, device=dev)
+    nt = torch.empty(n, dtype=torch.int32, device=dev)
+    ht = torch.empty(max(w.n_hits, 1), dtype=torch.int32, device=dev)
+    st = torch.empty(n, dtype=torch.int32, device=dev)
+    hs = f.hits_struct(hits)
+    hough.hough_find_iterative(f.ctx, hs, offs[:n + 1], n, mt, tr, nt, ht, st, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    hough.hough_find_iterative(f.ctx, hs, offs[:n + 1], n, mt, tr, nt, ht, st, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ntv = nt.cpu().numpy()
+    trv = tr.cpu().numpy().view(hough.ITER_DTYPE).reshape(n, mt)
+    pk = hough.decode_peaks(out_find["peaks"])
+    npk = out_find["n_peaks"].cpu().numpy()
+    match = total = 0
+    for k in range(n):
+        peaks = {(int(x["theta"]), int(x["rho"])) for x in pk[k][:npk[k]]}
+        for j in range(ntv[k]):
+            total += 1
+            match += (int(trv[k][j]["theta"]), int(trv[k][j]["rho"])) in peaks
+    f.close()
+    return {"method": "iterative highest bin: vote, argmax, take its line's hits, re-vote",
+            "windows": n, "ms": round(ms, 3), "windows_per_s": round(n / (ms * 1e-3), 1),
+            "mean_tracks_per_window": round(float(ntv.mean()), 2),
+            "tracks_that_are_local_max_peaks": round(match / max(total, 1), 4)}
+
+
 def _coarse_fine_leg(args, dev, stream, flush, w, hits, offs):
     """The paper's own two-stage search (coarse 18 x 100, then 10 x 10 of the
     180 x 1000 grid; one line per window) on the same batch, and how often its
@@ -612,6 +652,8 @@ def run_ours(args):
             if args.slice_us > 0 else None
         coarse_fine = _coarse_fine_leg(args, dev, stream, flush, w, hits, offs) \
             if args.coarse_fine else None
+        iterative = _iterative_leg(args, dev, stream, w, hits, offs, out) \
+            if args.iter_windows > 0 else None
         result = {
             "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
@@ -641,6 +683,7 @@ def run_ours(args):
             "serving": serving,
             "time_slicing": slicing,
             "coarse_to_fine": coarse_fine,
+            "iterative": iterative,
             "latency_us": {"p50": serving["p50_us"], "p99": serving["p99_us"],
                            "source": "serving leg"} if serving else None,
             "cpu_baseline": cpu,
@@ -699,6 +742,7 @@ def main():
                     help="threads,word_rows,hit_stage,ctas_per_sm for the serving context")
     ap.add_argument("--slice-us", type=float, default=100.0)
     ap.add_argument("--no-coarse-fine", dest="coarse_fine", action="store_false")
+    ap.add_argument("--iter-windows", type=int, default=20000)
     ap.add_argument("--slice-rate", type=float, default=0.6)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the library's default launch shape instead of autotuning it")

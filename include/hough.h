@@ -58,6 +58,7 @@ typedef enum hough_status {
 #define HOUGH_WIN_HIT_OUT_OF_RANGE 2u  /* a hit lies outside the detector box; ignored   */
 #define HOUGH_WIN_VOTE_OUT_OF_RANGE 4u /* a valid hit's vote fell outside [0, n_rho)    */
 #define HOUGH_WIN_BAD_OFFSETS 8u       /* offsets not ordered or beyond n_hits; skipped  */
+#define HOUGH_WIN_TOO_LARGE 16u        /* more valid hits than the entry point stages    */
 
 /* hough_thresholds.flags */
 #define HOUGH_FLAG_EXPORT_ACC 1u /* write the full int32 accumulator (tracks_out->acc) */
@@ -246,6 +247,39 @@ typedef struct hough_line {
 int hough_find_coarse_fine(hough_ctx *ctx, const hough_hits *hits, const int64_t *window_offsets,
                            int64_t n_windows, hough_line *lines, int32_t *hit_track,
                            void *stream);
+
+/*
+ * Iterative highest-bin search (the literal reading of the paper's peak step,
+ * Section 4: the bin with the highest accumulation is the most probable
+ * line, Section 5: its seeds are the hits aligned with it; repeated until no
+ * line is left).  Per window: vote the hits not yet assigned into the full
+ * n_theta x n_rho accumulator, take its highest bin (ties: first in
+ * row-major order), stop if it holds fewer than vote_threshold votes, else
+ * give track k every remaining hit whose bin in that row is within
+ * assoc_tol_bins of it, remove them and vote again; at most max_tracks
+ * tracks (1..HOUGH_MAX_PEAKS).  Same fixed-point arithmetic as hough_find.
+ *   tracks[n_windows * max_tracks]  device, per track (theta, rho, votes,
+ *                                   n_hits);
+ *   n_tracks[n_windows]             device, tracks found;
+ *   hit_track[n_hits]               device, track index, -1 if none, -2
+ *                                   outside the detector box;
+ *   window_status[n_windows]        device, HOUGH_WIN_* flags; a window with
+ *                                   more than HOUGH_ITER_MAX_HITS valid hits
+ *                                   gets HOUGH_WIN_TOO_LARGE and no track.
+ * Hits and offsets as hough_find.  Asynchronous on stream.
+ * Errors: INVALID_ARG, UNSUPPORTED_SHAPE, CUDA.
+ */
+#define HOUGH_ITER_MAX_HITS 4096
+typedef struct hough_iter_track {
+    int32_t theta;
+    int32_t rho;
+    int32_t votes;
+    int32_t n_hits;
+} hough_iter_track;
+int hough_find_iterative(hough_ctx *ctx, const hough_hits *hits, const int64_t *window_offsets,
+                         int64_t n_windows, int32_t max_tracks, hough_iter_track *tracks,
+                         int32_t *n_tracks, int32_t *hit_track, uint32_t *window_status,
+                         void *stream);
 
 /*
  * Time slicing on the device (Section 5: the hits of a readout are divided

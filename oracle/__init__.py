@@ -31,6 +31,8 @@ CF_DTYPE = np.dtype([(k, "<i4") for k in ("coarse_theta", "coarse_rho", "coarse_
                                             "fine_theta", "fine_rho", "fine_votes", "n_seeds",
                                             "found")])
 
+ITER_DTYPE = np.dtype([(k, "<i4") for k in ("theta", "rho", "votes", "n_hits")])
+
 WIN_PEAK_OVERFLOW = 1
 WIN_HIT_OUT_OF_RANGE = 2
 WIN_VOTE_OUT_OF_RANGE = 4
@@ -89,6 +91,8 @@ def _load():
         lib.oracle_coarse_fine_window.restype = i32
         lib.oracle_coarse_fine_batch.argtypes = [P, P, P, P, P, i64, P, P]
         lib.oracle_coarse_fine_batch.restype = i32
+        lib.oracle_iterative_batch.argtypes = [P, i32, i32, P, P, P, P, i64, i32, P, P, P]
+        lib.oracle_iterative_batch.restype = i32
         _lib = lib
     return _lib
 
@@ -266,3 +270,26 @@ def coarse_fine(geom: dict, phi_q, z_q, offsets, vote_threshold=5, assoc_tol_bin
     if rc != 0:
         raise ValueError("oracle_coarse_fine_batch: bad arguments")
     return out, ht[:len(phi_q)]
+
+
+def iterative(geom: dict, n_theta: int, n_rho: int, phi_q, z_q, offsets, max_tracks=64,
+              vote_threshold=5, assoc_tol_bins=1):
+    """Highest bin, assign its line's hits, remove them, vote again (the literal
+    reading of the paper's peak step): (tracks[n_windows, max_tracks] ITER_DTYPE,
+    n_tracks[n_windows], hit_track[n_hits])."""
+    lib = _load()
+    g = make_geometry(geom)
+    th = make_thresholds(vote_threshold, assoc_tol_bins, 0)
+    phi_q = np.ascontiguousarray(phi_q, np.int32)
+    z_q = np.ascontiguousarray(z_q, np.int32)
+    offsets = np.ascontiguousarray(offsets, np.int64)
+    nw = len(offsets) - 1
+    tracks = np.zeros((nw, max(max_tracks, 1)), ITER_DTYPE)
+    n_tracks = np.zeros(nw, np.int32)
+    ht = np.zeros(max(len(phi_q), 1), np.int32)
+    rc = lib.oracle_iterative_batch(ctypes.byref(g), n_theta, n_rho, ctypes.byref(th), _ptr(phi_q),
+                                    _ptr(z_q), _ptr(offsets), nw, max_tracks, _ptr(tracks),
+                                    _ptr(n_tracks), _ptr(ht))
+    if rc != 0:
+        raise ValueError("oracle_iterative_batch: bad arguments")
+    return tracks, n_tracks, ht[:len(phi_q)]

@@ -28,6 +28,9 @@
  *      grouped per peak.
  * and, before all of these, the time slicing of a readout into overlapping
  * windows (Section 5: 10 ns windows sliding by 5 ns; oracle_time_slice).
+ * Two variants of steps C-D: the paper's coarse-to-fine search for one line
+ * (oracle_coarse_fine_*) and the iterative highest-bin search
+ * (oracle_iterative_*).
  * The readings of the points the paper leaves open (units, theta sampling,
  * fixed-point tables, threshold, tie-break, tolerance) are listed in the
  * design notes of the repository.
@@ -609,6 +612,104 @@ int oracle_coarse_fine_batch(const oracle_geometry *g, const oracle_thresholds *
             return -1;
         int rc = oracle_coarse_fine_window(g, th, phi_q + b, z_q + b, e - b, out + w,
                                            hit_track + b);
+        if (rc != 0)
+            return rc;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------ iterative single peak */
+
+/*
+ * The literal reading of the paper's peak step (Section 4: the bin with the
+ * highest accumulation is the most probable line; Section 5: the seeds are
+ * the hits aligned with it), repeated until no line is left: vote the hits
+ * not yet assigned into the full accumulator, take its highest bin (ties:
+ * first in row-major order), stop if it holds fewer than T votes, else give
+ * track k every remaining hit whose bin in that row is within tol of it,
+ * remove them and vote again.  At most max_tracks tracks.
+ * Per window: tracks[k] = (theta, rho, votes, n_hits), n_tracks, and per hit
+ * its track index, -1 if none, -2 outside the detector box.
+ */
+typedef struct {
+    int32_t theta, rho, votes, n_hits;
+} oracle_iter_track;
+
+int oracle_iterative_window(const oracle_geometry *g, int n_theta, int n_rho,
+                            const oracle_thresholds *th, const int32_t *phi_q, const int32_t *z_q,
+                            int64_t n, int max_tracks, oracle_iter_track *tracks,
+                            int32_t *n_tracks, int32_t *hit_track)
+{
+    int32_t *C = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_theta);
+    int32_t *S = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_theta);
+    int32_t *acc = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_theta * (size_t)n_rho);
+    int64_t D = 0;
+    int k = oracle_tables(g, n_theta, n_rho, C, S, &D);
+    if (k < 0 || !C || !S || !acc || max_tracks < 0) {
+        free(C);
+        free(S);
+        free(acc);
+        return -1;
+    }
+    for (int64_t h = 0; h < n; ++h)
+        hit_track[h] = hit_is_valid(g, phi_q[h], z_q[h]) ? -1 : -2;
+    int found = 0;
+    while (found < max_tracks) {
+        memset(acc, 0, sizeof(int32_t) * (size_t)n_theta * (size_t)n_rho);
+        for (int64_t h = 0; h < n; ++h) {
+            if (hit_track[h] != -1)
+                continue;
+            for (int t = 0; t < n_theta; ++t) {
+                int64_t b = rho_bin(phi_q[h], z_q[h], C[t], S[t], D, k);
+                if (b >= 0 && b < n_rho)
+                    acc[(size_t)t * n_rho + b] += 1;
+            }
+        }
+        int bt = 0, bb = 0;
+        for (int t = 0; t < n_theta; ++t)
+            for (int b = 0; b < n_rho; ++b)
+                if (acc[(size_t)t * n_rho + b] > acc[(size_t)bt * n_rho + bb]) {
+                    bt = t;
+                    bb = b;
+                }
+        int32_t votes = acc[(size_t)bt * n_rho + bb];
+        if (votes < th->vote_threshold)
+            break;
+        int32_t taken = 0;
+        for (int64_t h = 0; h < n; ++h) {
+            if (hit_track[h] != -1)
+                continue;
+            int64_t b = rho_bin(phi_q[h], z_q[h], C[bt], S[bt], D, k);
+            if (b - bb <= th->assoc_tol_bins && bb - b <= th->assoc_tol_bins) {
+                hit_track[h] = found;
+                ++taken;
+            }
+        }
+        tracks[found].theta = bt;
+        tracks[found].rho = bb;
+        tracks[found].votes = votes;
+        tracks[found].n_hits = taken;
+        ++found;
+    }
+    *n_tracks = found;
+    free(C);
+    free(S);
+    free(acc);
+    return 0;
+}
+
+int oracle_iterative_batch(const oracle_geometry *g, int n_theta, int n_rho,
+                           const oracle_thresholds *th, const int32_t *phi_q, const int32_t *z_q,
+                           const int64_t *offsets, int64_t n_windows, int max_tracks,
+                           oracle_iter_track *tracks, int32_t *n_tracks, int32_t *hit_track)
+{
+    for (int64_t w = 0; w < n_windows; ++w) {
+        int64_t b = offsets[w], e = offsets[w + 1];
+        if (b < 0 || e < b)
+            return -1;
+        int rc = oracle_iterative_window(g, n_theta, n_rho, th, phi_q + b, z_q + b, e - b,
+                                         max_tracks, tracks + (size_t)w * max_tracks,
+                                         n_tracks + w, hit_track + b);
         if (rc != 0)
             return rc;
     }

@@ -20,6 +20,7 @@
 #include "hough_internal.h"
 #include "hough_kernels.cuh"
 #include "hough_coarse_fine.cuh"
+#include "hough_iterative.cuh"
 
 // Whether every valid hit votes inside [0, n_rho) in every row: the bin is
 // monotone in phi and in z, so the four corners of the detector box bound it.
@@ -654,6 +655,49 @@ int hough_find_coarse_fine(hough_ctx *ctx, const hough_hits *hits, const int64_t
     p.hit_track = hit_track;
     const long long blocks = std::min<long long>(n_windows, (long long)ctx->num_sms * 8);
     hk::coarse_fine_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(p);
+    if (cudaGetLastError() != cudaSuccess)
+        return fail(ctx, HOUGH_ERR_CUDA);
+    ctx->launches += 1;
+    return HOUGH_OK;
+}
+
+int hough_find_iterative(hough_ctx *ctx, const hough_hits *hits, const int64_t *window_offsets,
+                         int64_t n_windows, int32_t max_tracks, hough_iter_track *tracks,
+                         int32_t *n_tracks, int32_t *hit_track, uint32_t *window_status,
+                         void *stream)
+{
+    if (!ctx || !hits_ok(hits) || n_windows < 0 || max_tracks < 1 ||
+        max_tracks > HOUGH_MAX_PEAKS ||
+        (n_windows > 0 && (!window_offsets || !tracks || !n_tracks || !window_status)) ||
+        (hits->n_hits > 0 && !hit_track) || n_windows >= (1ll << 31) - 65536)
+        return fail(ctx, HOUGH_ERR_INVALID_ARG);
+    if (n_windows == 0)
+        return HOUGH_OK;
+    // 512 threads, the largest tile that fits beside the stage of hits
+    hough_launch l{512, 32, HOUGH_ITER_MAX_HITS, 1};
+    const size_t stage = (size_t)HOUGH_ITER_MAX_HITS * 12;
+    for (int wr : {128, 64}) {
+        if ((size_t)wr * ctx->n_rho * 4 + stage <= ctx->smem_optin && ctx->n_theta >= 2 * wr) {
+            l.word_rows = wr;
+            break;
+        }
+    }
+    const size_t smem = (size_t)l.word_rows * ctx->n_rho * 4 + stage;
+    if (smem > ctx->smem_optin)
+        return fail(ctx, HOUGH_ERR_UNSUPPORTED_SHAPE);
+    if (cudaFuncSetAttribute(hk::iterative_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return fail(ctx, HOUGH_ERR_CUDA);
+    hough_tracks out{};
+    out.hit_track = hit_track;
+    out.window_status = window_status;
+    hk::IterParams q{};
+    q.k = make_params(ctx, hits, window_offsets, n_windows, &out, nullptr, l);
+    q.max_tracks = max_tracks;
+    q.tracks = reinterpret_cast<int4 *>(tracks);
+    q.n_tracks = n_tracks;
+    const long long grid = std::min<long long>(n_windows, (long long)ctx->num_sms);
+    hk::iterative_kernel<<<(unsigned)grid, 512, smem, (cudaStream_t)stream>>>(q);
     if (cudaGetLastError() != cudaSuccess)
         return fail(ctx, HOUGH_ERR_CUDA);
     ctx->launches += 1;

@@ -45,6 +45,7 @@
 namespace hk {
 
 constexpr int kSegPk = 64;      // peak-key segment per warp; merged when past 32 entries
+constexpr int kSegRoom = 32;    // appends one check step can make per warp (1 per lane)
 constexpr int kMergeStage = 4 * HOUGH_MAX_PEAKS * 4 / 8;   // merge staging keys (the pk area)
 constexpr unsigned long long kKeyMax = ~0ull;
 
@@ -785,7 +786,7 @@ __device__ void check_direct(const KParams &p, const TileView<P> &tv, int rlo, i
         record_peaks(peak, v, t, b, ps);
         if (lane == 0)
             wc.n_pk[warp] = ps.n;
-        if (__syncthreads_or(lane == 0 && ps.n > ps.cap - 32)) {
+        if (__syncthreads_or(lane == 0 && ps.n > ps.cap - kSegRoom)) {
             merge_peaks(p, keys, top_stage, seg_cap, wc, vh, ws);
             ps.n = 0;
             ps.kth = ws.kth;
@@ -915,9 +916,11 @@ __device__ int process_tiles(const KParams &p, long long beg, int H, uint32_t *a
                         cmp[(y - yl) + ((yl & (nw - 1)) << 5) + (yl >> lnw)] = e;
                     }
                 };
-                for (int j = 0; j < cnt; ++j)
+                // only this round's entries: [base, base + hi) of the order
+                for (int j = max(0, base - my_pre); j < min(cnt, base + hi - my_pre); ++j)
                     put(my_pre + j - base, my_cl[j * 32 + lane]);
-                for (int j = lane; j < n_ovf_w; j += 32)          // the whole warp
+                for (int j = max(0, base - ovf_pre) + lane; j < min(n_ovf_w, base + hi - ovf_pre);
+                     j += 32)                                     // the whole warp
                     put(ovf_pre + j - base, my_cl[L * 32 + j]);
                 __syncthreads();
                 for (int c0 = 0; c0 < hi; c0 += B) {
@@ -931,7 +934,7 @@ __device__ int process_tiles(const KParams &p, long long beg, int H, uint32_t *a
                     record_peaks(peak, v, t0 + i, b, ps);
                     if (lane == 0)
                         wc.n_pk[warp] = ps.n;
-                    if (__syncthreads_or(lane == 0 && ps.n > seg_cap - 32)) {
+                    if (__syncthreads_or(lane == 0 && ps.n > seg_cap - kSegRoom)) {
                         merge_peaks(p, keys, top_stage, seg_cap, wc, vh, ws);
                         ps.n = 0;
                         ps.kth = ws.kth;
@@ -948,7 +951,7 @@ __device__ int process_tiles(const KParams &p, long long beg, int H, uint32_t *a
             wc.n_found[warp] += ps.found;
         }
         // keep room for a full step of appends in every segment
-        if (__syncthreads_or(lane == 0 && ps.n > seg_cap - 32))
+        if (__syncthreads_or(lane == 0 && ps.n > seg_cap - kSegRoom))
             merge_peaks(p, keys, top_stage, seg_cap, wc, vh, ws);
         if (!last) {
             for (int b = threadIdx.x; b < p.n_rho; b += blockDim.x) {

@@ -26,6 +26,8 @@ HOUGH_WIN_PEAK_OVERFLOW = 1
 HOUGH_WIN_HIT_OUT_OF_RANGE = 2
 HOUGH_WIN_VOTE_OUT_OF_RANGE = 4
 HOUGH_WIN_BAD_OFFSETS = 8
+HOUGH_WIN_TOO_LARGE = 16
+HOUGH_ITER_MAX_HITS = 4096
 HOUGH_FLAG_EXPORT_ACC = 1
 HOUGH_ERR_TIMEOUT = -4
 HOUGH_ERR_UNSUPPORTED_SHAPE = -5
@@ -141,6 +143,7 @@ def load(build_if_missing: bool = False):
         "hough_last_error": ([P], i32),
         "hough_launch_count": ([P], i64),
         "hough_find_coarse_fine": ([P, P, P, i64, P, P, P], i32),
+        "hough_find_iterative": ([P, P, P, i64, ctypes.c_int32, P, P, P, P, P], i32),
         "hough_time_slice": ([P, P, P, P, i64, i64, i64, i64, i64, P, P, P, i64, P, P, P], i32),
         "hough_server_create": ([P, P, P], i32),
         "hough_server_submit": ([P, P, P], i32),
@@ -254,6 +257,18 @@ def hough_find_coarse_fine(ctx, hits: hough_hits, window_offsets, n_windows: int
     _check(load().hough_find_coarse_fine(ctx, ctypes.byref(hits), _ptr(window_offsets), n_windows,
                                          _ptr(lines), _ptr(hit_track), _stream(stream)),
            "hough_find_coarse_fine")
+
+
+ITER_DTYPE = np.dtype([(k, "<i4") for k in ("theta", "rho", "votes", "n_hits")])
+
+
+def hough_find_iterative(ctx, hits: hough_hits, window_offsets, n_windows: int, max_tracks: int,
+                         tracks, n_tracks, hit_track, window_status, stream=None) -> None:
+    """Iterative highest-bin search; tracks: int32 tensor [n_windows, max_tracks, 4]."""
+    _check(load().hough_find_iterative(ctx, ctypes.byref(hits), _ptr(window_offsets), n_windows,
+                                       max_tracks, _ptr(tracks), _ptr(n_tracks), _ptr(hit_track),
+                                       _ptr(window_status), _stream(stream)),
+           "hough_find_iterative")
 
 
 def hough_time_slice(ctx, t, in0, in1, t0: int, step: int, length: int, n_windows: int,
