@@ -954,9 +954,13 @@ __device__ int process_tiles(const KParams &p, long long beg, int H, uint32_t *a
         if (__syncthreads_or(lane == 0 && ps.n > seg_cap - kSegRoom))
             merge_peaks(p, keys, top_stage, seg_cap, wc, vh, ws);
         if (!last) {
-            for (int b = threadIdx.x; b < p.n_rho; b += blockDim.x) {
-                carry0[b] = tile_val<P>(acc, p.n_rho, p.lw, R - 2, b);
-                carry1[b] = tile_val<P>(acc, p.n_rho, p.lw, R - 1, b);
+            // rows R-2 and R-1 are two word rows, i.e. two banks: half of a
+            // warp reads each, so every wavefront serves both banks
+            for (int x = threadIdx.x; x < ((p.n_rho + 15) >> 4) << 5; x += blockDim.x) {
+                const int r = (x >> 4) & 1;
+                const int b = ((x >> 5) << 4) | (x & 15);
+                if (b < p.n_rho)
+                    (r ? carry1 : carry0)[b] = tile_val<P>(acc, p.n_rho, p.lw, R - 2 + r, b);
             }
         }
         __syncthreads();
