@@ -403,7 +403,9 @@ int hough_find_noalloc(const hough_geometry *g, int n_theta, int n_rho,
  *
  * While a server exists it owns its context: make no other call on that
  * context (hough_find, hough_set_launch, ...) until hough_server_destroy.
- * Server calls may be made from any host thread.
+ * Server calls may be made from any host thread.  While batches are on the
+ * GPU the worker polls their completion events (yielding between polls), so
+ * it keeps one host core busy; it sleeps when nothing is queued or running.
  */
 typedef struct hough_server hough_server;
 

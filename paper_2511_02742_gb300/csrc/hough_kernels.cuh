@@ -120,7 +120,7 @@ __host__ __device__ inline SmemLayout smem_layout(int word_rows, int hit_stage, 
     L.cnt = off;                                    // counts + cursors per category
     off = align_up(off + (size_t)2 * (HOUGH_MAX_PEAKS + 2) * 4, 16);
     L.hist = off;                                   // per-warp counters (WarpCounters)
-    off = align_up(off + (size_t)6 * 32 * 4, 16);
+    off = align_up(off + (size_t)5 * 32 * 4, 16);
     L.vh = off;                                     // per-warp peak-vote histograms
     off = align_up(off + (size_t)n_warps * 64 * 4, 16);
     L.wtot = off;
@@ -133,7 +133,6 @@ struct WinScalars {
     unsigned long long kth;   // a peak enters a segment only if its key < kth
     int n_top;                // kept peaks in keys[0 .. n_top)
     int n_sel;                // entries gathered for a merge
-    int seg_ovf;              // a warp's candidate list overflowed in this tile
     int vk;                   // lower bound of the k-th best vote count
     int n_keep_top;           // kept-list entries with >= vk votes (merging)
     unsigned int flags;       // HOUGH_WIN_* for this window
@@ -145,9 +144,7 @@ struct WarpCounters {
     int *n_cl;      // candidate-list entries of the warp in this tile
     int *n_pk;      // peaks in the warp's segment since the last merge
     int *n_found;   // local maxima >= T found by the warp in this window
-    int *pre_cl;    // exclusive prefix of n_cl (spreading the check over warps)
-    int *pre_pk;    // exclusive prefix of n_pk (merging); separate from pre_cl
-                    // because a merge can run in the middle of the check
+    int *pre_pk;    // exclusive prefix of n_pk (merging)
     int *n_ovf;     // entries the warp's lanes sent to its overflow area in this tile
 };
 
@@ -306,10 +303,28 @@ __device__ void vote_tile(const KParams &p, uint32_t *acc, const int2 *stage, in
 #pragma unroll
         for (int k = 0; k < P; ++k)
             old[k] = in[k] ? atom_add_shared(col + (unsigned)bb[k] * 128u, 1u << (k * CW)) : 0u;
+        if (P == 4) {
+            // four fields: one xor-and test per vote, one branch per hit
+            unsigned hit = 0u;
 #pragma unroll
-        for (int k = 0; k < P; ++k)
-            if (in[k] && ((old[k] >> (k * CW)) & MASK) == tm1)
-                list_append(seg, L, cnt, ovf, ((col_word0 + (unsigned)bb[k] * 32u) << 2) | (unsigned)k);
+            for (int k = 0; k < P; ++k) {
+                const unsigned mk = MASK << (k * CW), tk = tm1 << (k * CW);
+                hit |= (in[k] && ((old[k] ^ tk) & mk) == 0u) ? (1u << k) : 0u;
+            }
+            if (hit) {
+#pragma unroll
+                for (int k = 0; k < P; ++k)
+                    if (hit & (1u << k))
+                        list_append(seg, L, cnt, ovf,
+                                    ((col_word0 + (unsigned)bb[k] * 32u) << 2) | (unsigned)k);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < P; ++k)
+                if (in[k] && ((old[k] >> (k * CW)) & MASK) == tm1)
+                    list_append(seg, L, cnt, ovf,
+                                ((col_word0 + (unsigned)bb[k] * 32u) << 2) | (unsigned)k);
+        }
     }
     if (oor)
         atomicOr(&ws.flags, HOUGH_WIN_VOTE_OUT_OF_RANGE);
@@ -832,6 +847,10 @@ __device__ int process_tiles(const KParams &p, long long beg, int H, uint32_t *a
         const int L = (p.seg_cl - p.seg_ovf) >> 5;
         const ListOvf ovf{wc.n_ovf + warp, p.seg_ovf};
         const bool fast = p.in_range && t0 + R <= p.n_theta;
+        TileView<P> tv{acc, carry0, carry1, t0, R, p.lw, p.n_theta, p.n_rho};
+        const int rlo = max(t0 - 1, 0);
+        const int rhi = last ? p.n_theta : t0 + R - 1;
+        const int ihi = rhi - t0;
         if (single) {
             if (fast)
                 vote_tile<P, true>(p, acc, stage, nv, t0, my_cl, L, cnt, ovf, ws);
@@ -845,22 +864,20 @@ __device__ int process_tiles(const KParams &p, long long beg, int H, uint32_t *a
                 __syncthreads();
             }
         }
+        // the carried row's candidates (it is complete since the previous
+        // tile) join the lists before the barrier that ends the vote
+        list_carry<P>(p, tv, rlo, rhi, my_cl, L, cnt, ovf);
         __syncthreads();
 
         if (p.export_acc)
             export_tile<P>(p, acc, t0, R, w);
-
-        TileView<P> tv{acc, carry0, carry1, t0, R, p.lw, p.n_theta, p.n_rho};
-        const int rlo = max(t0 - 1, 0);
-        const int rhi = last ? p.n_theta : t0 + R - 1;
-        const int ihi = rhi - t0;
-        list_carry<P>(p, tv, rlo, rhi, my_cl, L, cnt, ovf);
-        __syncthreads();
         // block-wide exclusive prefix: a warp's entries are its lanes' column
         // entries in lane order, then its overflow entries (only an overflow
         // area past its capacity sends the tile to the direct test)
         int my_pre = 0;             // index of this lane's first column entry
         int ovf_pre = 0, n_ovf_w = 0;   // index and number of the warp's overflow entries
+        int total = 0;              // entries of the block
+        bool lost;                  // an overflow area overflowed: direct test
         {
             const int n_ovf = wc.n_ovf[warp];
             n_ovf_w = min(n_ovf, p.seg_ovf);
@@ -874,30 +891,24 @@ __device__ int process_tiles(const KParams &p, long long beg, int H, uint32_t *a
             }
             if (lane == 31)
                 wc.n_cl[warp] = incl + n_ovf_w;
-            const bool lost = __syncthreads_or(lane == 0 && n_ovf > p.seg_ovf);
-            if (warp == 0) {
-                const int wt = lane < nw ? wc.n_cl[lane] : 0;
-                int wi = wt;
+            lost = __syncthreads_or(lane == 0 && n_ovf > p.seg_ovf);
+            // every warp scans the warp totals itself (one barrier in all)
+            const int wt = lane < nw ? wc.n_cl[lane] : 0;
+            int wi = wt;
 #pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const int y = __shfl_up_sync(0xffffffffu, wi, d);
-                    if (lane >= d)
-                        wi += y;
-                }
-                if (lane < nw)
-                    wc.pre_cl[lane] = wi - wt;
-                if (lane == 31) {
-                    ws.n_sel = wi;
-                    ws.seg_ovf = lost ? 1 : 0;
-                }
+            for (int d = 1; d < 32; d <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, wi, d);
+                if (lane >= d)
+                    wi += y;
             }
-            __syncthreads();
-            my_pre = wc.pre_cl[warp] + incl - c;
-            ovf_pre = wc.pre_cl[warp] + __shfl_sync(0xffffffffu, incl, 31);
+            const int pre_w = __shfl_sync(0xffffffffu, wi - wt, warp);
+            total = __shfl_sync(0xffffffffu, wi, 31);
+            my_pre = pre_w + incl - c;
+            ovf_pre = pre_w + __shfl_sync(0xffffffffu, incl, 31);
         }
         PeakSink ps{keys + p.kp + (size_t)warp * seg_cap, seg_cap, wc.n_pk[warp], 0, ws.kth,
                     ws.vk, vh + warp * kHistBins};
-        if (!ws.seg_ovf) {
+        if (!lost) {
             // One thread per listed entry, all warps evenly loaded.  The
             // entries are first gathered into cmp in a transposed order:
             // within each block-sized chunk, entry y of the compact order
@@ -906,7 +917,6 @@ __device__ int process_tiles(const KParams &p, long long beg, int H, uint32_t *a
             // hold entries of 32 different owners, whose word rows, and so
             // whose tile banks, differ.  cmp holds p.cmp_cap entries; larger
             // lists are taken in rounds.
-            const int total = ws.n_sel;
             const int B = blockDim.x, lnw = __ffs(nw) - 1;
             for (int base = 0; base < total; base += p.cmp_cap) {
                 const int hi = min(total - base, p.cmp_cap);
@@ -941,7 +951,8 @@ __device__ int process_tiles(const KParams &p, long long beg, int H, uint32_t *a
                         ps.vk = ws.vk;
                     }
                 }
-                __syncthreads();
+                if (base + p.cmp_cap < total)
+                    __syncthreads();            // the next round rewrites cmp
             }
         } else {
             check_direct<P>(p, tv, rlo, rhi, ps, keys, top_stage, seg_cap, wc, vh, ws);
@@ -950,9 +961,8 @@ __device__ int process_tiles(const KParams &p, long long beg, int H, uint32_t *a
             wc.n_pk[warp] = ps.n;
             wc.n_found[warp] += ps.found;
         }
-        // keep room for a full step of appends in every segment
-        if (__syncthreads_or(lane == 0 && ps.n > seg_cap - kSegRoom))
-            merge_peaks(p, keys, top_stage, seg_cap, wc, vh, ws);
+        // every check step ended in a barrier, so the carried rows are no
+        // longer read: save this tile's last two rows for the next one
         if (!last) {
             // rows R-2 and R-1 are two word rows, i.e. two banks: half of a
             // warp reads each, so every wavefront serves both banks
@@ -963,7 +973,10 @@ __device__ int process_tiles(const KParams &p, long long beg, int H, uint32_t *a
                     (r ? carry1 : carry0)[b] = tile_val<P>(acc, p.n_rho, p.lw, R - 2 + r, b);
             }
         }
-        __syncthreads();
+        // keep room for a full step of appends in every segment; this
+        // barrier also ends the tile (the next one clears the accumulator)
+        if (__syncthreads_or(lane == 0 && ps.n > seg_cap - kSegRoom))
+            merge_peaks(p, keys, top_stage, seg_cap, wc, vh, ws);
     }
     int pending = 0;
     for (int k = 0; k < nw; ++k)
@@ -1135,7 +1148,7 @@ __global__ void __launch_bounds__(1024, 1) find_kernel(KParams p)
     unsigned long long *top_stage = reinterpret_cast<unsigned long long *>(smem + L.pk);
     int *cnt = reinterpret_cast<int *>(smem + L.cnt);
     int *wcnt = reinterpret_cast<int *>(smem + L.hist);
-    WarpCounters wc{wcnt, wcnt + 32, wcnt + 64, wcnt + 96, wcnt + 128, wcnt + 160};
+    WarpCounters wc{wcnt, wcnt + 32, wcnt + 64, wcnt + 96, wcnt + 128};
     int *vh = reinterpret_cast<int *>(smem + L.vh);
     int *wtot = reinterpret_cast<int *>(smem + L.wtot);
 
@@ -1155,7 +1168,6 @@ __global__ void __launch_bounds__(1024, 1) find_kernel(KParams p)
             if (threadIdx.x == 0) {
                 ws.kth = p.max_peaks > 0 ? kKeyMax : 0ull;
                 ws.n_top = 0;
-                ws.seg_ovf = 0;
                 ws.vk = 0;
                 ws.flags = 0u;
             }

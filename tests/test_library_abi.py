@@ -96,6 +96,27 @@ def test_null_pointers_are_rejected(lib):
     assert lib.hough_launch_count(None) == 0
     C = np.zeros(4, np.int32)
     assert lib.hough_tables(None, 4, 4, C.ctypes.data_as(ctypes.c_void_p), None, None, None) == -1
+    # the other entry points check their context and sizes before anything else
+    assert lib.hough_find_host(None, None, None, 0, None, None) == -1
+    assert lib.hough_encode(None, None, None, 0, None, None, None) == -1
+    assert lib.hough_find_coarse_fine(None, None, None, 0, None, None, None) == -1
+    assert lib.hough_find_iterative(None, None, None, 0, 1, None, None, None, None, None) == -1
+    assert lib.hough_time_slice(None, None, None, None, 0, 0, 5, 10, 1, None, None, None, 0,
+                                None, None, None) == -1
+    assert lib.hough_plan_create(None, None, None, 0, None, None, None) == -1
+    assert lib.hough_autotune(None, None, None, 0, None, None, 1, None) == -1
+    assert lib.hough_set_launch(None, None) == -1
+    assert lib.hough_get_launch(None, None) == -1
+    # the request loop: every call checks its server first; destroy is NULL-safe
+    res = (ctypes.c_int64 * 8)()
+    assert lib.hough_server_create(None, None, None) == -1
+    assert lib.hough_server_submit(None, None, None) == -1
+    assert lib.hough_server_wait(None, 1, 0, None) == -1
+    assert lib.hough_server_poll(None, None, 0, ctypes.cast(res, ctypes.c_void_p)) == -1
+    assert lib.hough_server_drain(None, 0) == -1
+    assert lib.hough_server_get_stats(None, None) == -1
+    lib.hough_server_destroy(None)
+    assert lib.hough_server_clock_ns() > 0
 
 
 def test_no_device_is_reported_not_faked(lib):
