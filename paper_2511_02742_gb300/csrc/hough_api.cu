@@ -65,6 +65,10 @@ struct hough_plan {
 
 namespace {
 
+// Static shared memory of the find kernel (its per-window scalars), rounded
+// up; checked against the compiled kernel in prepare_find.
+constexpr size_t kStaticSmemReserve = 256;
+
 int fail(hough_ctx *ctx, int code)
 {
     if (ctx && code != HOUGH_OK)
@@ -101,7 +105,10 @@ int next_pow2(int x)
 int cl_entries_for(const hough_ctx *ctx, int word_rows, int hit_stage, int ctas, int threads)
 {
     const int nw = threads / 32;
-    const size_t budget = std::min(ctx->smem_optin, ctx->smem_per_sm / (size_t)ctas - 1024);
+    // per CTA the SM also reserves 1 KB and holds the kernel's static shared
+    // variables (kStaticSmemReserve covers them): `ctas` CTAs must fit
+    const size_t budget = std::min(ctx->smem_optin,
+                                   ctx->smem_per_sm / (size_t)ctas - 1024 - kStaticSmemReserve);
     hk::SmemLayout L0 = hk::smem_layout(word_rows, hit_stage, ctx->n_rho, 0, nw);
     long long room = L0.total < budget ? (long long)((budget - L0.total) / 4) : 0;
     // lists able to hold every counter of the tile and of the carried row in
@@ -138,7 +145,8 @@ int resolve_launch(const hough_ctx *ctx, const hough_launch &in, hough_launch &o
         l.word_rows = 32;
         for (int wr : {128, 64}) {
             hk::SmemLayout L = hk::smem_layout(wr, l.hit_stage, ctx->n_rho, 4096, l.threads / 32);
-            if ((L.total + 1024) * (size_t)l.ctas_per_sm <= ctx->smem_per_sm && L.total <= ctx->smem_optin &&
+            if ((L.total + 1024 + kStaticSmemReserve) * (size_t)l.ctas_per_sm <= ctx->smem_per_sm &&
+                L.total <= ctx->smem_optin &&
                 ctx->n_theta >= 2 * wr) {
                 l.word_rows = wr;
                 break;
@@ -262,6 +270,10 @@ int prepare_find(hough_ctx *ctx, int64_t n_windows, const hough_launch &req, Pre
         return rc;
     if (cudaFuncSetAttribute(hk::find_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)pr.smem) != cudaSuccess)
+        return HOUGH_ERR_CUDA;
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, hk::find_kernel) != cudaSuccess ||
+        fa.sharedSizeBytes > kStaticSmemReserve)
         return HOUGH_ERR_CUDA;
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hk::find_kernel, pr.l.threads,
