@@ -320,10 +320,12 @@ def _serving_leg(args, dev):
     dt_ns = int(args.serve_slice_ms * 1e6)
     n_slices = int(round(args.serve_seconds * 1e3 / args.serve_slice_ms))
     counts = np.random.default_rng(11).poisson(args.serve_rate * dt_ns * 1e-9, n_slices)
-    if args.serve_launch:
-        hough.hough_set_launch(f.ctx, *[int(x) for x in args.serve_launch.split(",")])
-    launch_used = hough.hough_get_launch(f.ctx)
-    srv = hough.Server(f, n_slots=4, slot_windows=4096, slot_hits=1 << 21, max_queued=1 << 16)
+    launch = [int(x) for x in args.serve_launch.split(",")] if args.serve_launch else None
+    launch_used = (dict(zip(("threads", "word_rows", "hit_stage", "ctas_per_sm"), launch))
+                   if launch else "server default: 512 threads, 1 CTA per SM, largest tile, "
+                                  "2048-hit stage")
+    srv = hough.Server(f, n_slots=4, slot_windows=4096, slot_hits=1 << 21, max_queued=1 << 16,
+                       launch=launch)
     clock = hough.hough_server_clock_ns
     ranges, lat, bsz, bwin, wait, gpu = {}, [], [], [], [], []
     state = {"mism": 0, "done": 0, "last_done": 0}
