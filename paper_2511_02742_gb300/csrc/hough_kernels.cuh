@@ -740,41 +740,49 @@ __device__ void merge_peaks(const KParams &p, unsigned long long *keys,
     __syncthreads();
 }
 
-// Export mode: write the tile's rows as int32 to acc[w][t][b].  A warp takes
-// 32 word rows x 8 bins: each lane reads its own word row (one bank, no
-// conflict), then shuffles turn the 32 x 8 block around so that every store
-// instruction writes 8 consecutive bins of 4 rows (four whole 32-byte sectors).
+// Export mode: write the tile's rows as int32 to acc[w][t][b].  Lane = word
+// row (its own bank, so the loads are conflict-free): a warp takes 8 bins of
+// 32 word rows and writes each of the P rows of every word row as one whole
+// 32-byte sector (two 16-byte stores).  When the accumulator is not 16-byte
+// aligned the same values go out as plain 4-byte stores.
 template <int P>
 __device__ void export_tile(const KParams &p, const uint32_t *acc, int t0, int R, long long w)
 {
+    constexpr int CW = 32 / P;
+    constexpr unsigned MASK = P == 1 ? 0xffffffffu : ((1u << CW) - 1u);
     const int WR = p.word_rows, G = WR >> 5;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int nchunks = (p.n_rho + 7) >> 3;
+    const int nq = (p.n_rho + 7) >> 3;               // groups of 8 bins
     int32_t *out = p.acc + (size_t)w * p.n_theta * p.n_rho;
-    for (int item = warp; item < G * nchunks; item += nw) {
-        const int g = item / nchunks, b0 = (item - g * nchunks) * 8;
-        uint32_t v[8];
+    const bool vec = ((reinterpret_cast<uintptr_t>(p.acc) & 15u) == 0u);
+    for (int item = warp; item < G * nq; item += nw) {
+        const int g = item / nq, b0 = (item - g * nq) * 8;
+        const int wr = g * 32 + lane;
+        const int nb = min(8, p.n_rho - b0);            // 8, or 4 at a ragged end
+        const uint32_t *col = acc + (size_t)(g * p.n_rho + b0) * 32 + lane;
+        uint32_t wv[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j)
-            v[j] = (b0 + j < p.n_rho) ? acc[(g * p.n_rho + b0 + j) * 32 + lane] : 0u;
-        const int j = lane & 7;
-        const int b = b0 + j;
-#pragma unroll 1
-        for (int q = 0; q < 8; ++q) {
-            const int src = 4 * q + (lane >> 3);
-            uint32_t word = 0u;
+            wv[j] = j < nb ? col[j * 32] : 0u;
 #pragma unroll
-            for (int jj = 0; jj < 8; ++jj) {
-                uint32_t x = __shfl_sync(0xffffffffu, v[jj], src);
-                word = (j == jj) ? x : word;
-            }
-            const int wr = g * 32 + src;
+        for (int s = 0; s < P; ++s) {
+            const int t = t0 + s * WR + wr;
+            if (s * WR + wr >= R || t >= p.n_theta)
+                continue;
+            int v[8];
 #pragma unroll
-            for (int s = 0; s < P; ++s) {
-                const int i = s * WR + wr;
-                const int t = t0 + i;
-                if (i < R && t < p.n_theta && b < p.n_rho)
-                    out[(size_t)t * p.n_rho + b] = field<P>(word, s);
+            for (int j = 0; j < 8; ++j)
+                v[j] = (int)((wv[j] >> (s * CW)) & MASK);
+            int32_t *row = out + (size_t)t * p.n_rho + b0;
+            if (vec) {
+                *reinterpret_cast<int4 *>(row) = make_int4(v[0], v[1], v[2], v[3]);
+                if (nb == 8)
+                    *reinterpret_cast<int4 *>(row + 4) = make_int4(v[4], v[5], v[6], v[7]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (j < nb)
+                        row[j] = v[j];
             }
         }
     }

@@ -310,3 +310,23 @@ def test_encode_entry_point(hough):
     np.testing.assert_array_equal(phi.cpu().numpy(), rp)
     np.testing.assert_array_equal(z.cpu().numpy(), rz)
     f.close()
+
+
+def test_export_to_an_unaligned_accumulator(hough):
+    """An accumulator pointer that is not 16-byte aligned gets the same values
+    (the kernel then writes 4-byte words instead of 16-byte vectors)."""
+    import torch
+    w = synth.generate(30, ("poisson", 10, 1, 40), (100.0, 300.0), 0.02, seed=41)
+    f = _finder(hough, 96, 332, export_acc=True)
+    hits = dict(vane=torch.from_numpy(w.vane).cuda(), strip=torch.from_numpy(w.strip).cuda())
+    offs = torch.from_numpy(w.offsets).cuda()
+    a = f.find(hits, offs)
+    out = f.alloc_outputs(w.n_windows, w.n_hits)
+    buf = torch.full((w.n_windows * 96 * 332 + 1,), -5, dtype=torch.int32, device="cuda")
+    out["acc"] = buf[1:].view(w.n_windows, 96, 332)
+    assert out["acc"].data_ptr() % 16 == 4
+    f.find(hits, offs, out=out)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out["acc"].cpu().numpy(), a["acc"].cpu().numpy())
+    assert int(buf[0].item()) == -5
+    f.close()
