@@ -189,6 +189,83 @@ def _iterative_leg(args, dev, stream, w, hits, offs, out_find):
             "tracks_that_are_local_max_peaks": round(match / max(total, 1), 4)}
 
 
+def _extension_leg(args, dev, stream, flush, w, hits, offs, out_find, hbm_gbs):
+    """Track extension (seed of three hits on consecutive vanes, extrapolated
+    vane by vane) on the timed batch's own find output: its time, Section 7's
+    efficiency against the generator's truth on a sample of windows, and
+    parity of a few windows with the oracle."""
+    import torch
+    import oracle
+    from paper_2511_02742_gb300 import evaluate, hough, synth
+    cfg = synth.WORKLOADS[args.workload]
+    f = hough.Finder(cfg["n_theta"], cfg["n_rho"])
+    tol = args.ext_tol_strips * synth.GEOMETRY["z_pitch_u"]
+    ext = f.extend(hits, offs, out_find, tol, stream=stream)
+    for _ in range(2):
+        f.extend(hits, offs, out_find, tol, out=ext, stream=stream)
+    torch.cuda.synchronize()
+    steps = max(1, min(args.steps, 10))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for i in range(steps):
+        _flush_l2(flush)
+        ev[i][0].record(stream)
+        f.extend(hits, offs, out_find, tol, out=ext, stream=stream)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    f.close()
+    tr = ext["tracks"].cpu().numpy().view(hough.EXT_DTYPE).reshape(w.n_windows, -1)
+    npk = out_find["n_peaks"].cpu().numpy()
+    et = ext["ext_track"].cpu().numpy()[:w.n_hits]
+    eh = ext["ext_hits"].cpu().numpy()[:w.n_hits]
+    n_ext = int(sum((tr[k][:npk[k]]["n_hits"] > 0).sum() for k in range(w.n_windows)))
+    n_eff = min(w.n_windows, args.ext_eff_windows)
+    sub = w.subset(np.arange(n_eff))
+    eff = evaluate.efficiency(sub.vane, sub.track, sub.offsets, sub.track_offsets,
+                              et[:sub.n_hits])
+    # parity of the timed output with the oracle on a sample of windows
+    ids = np.random.default_rng(4).choice(w.n_windows, 20, replace=False)
+    phi, z = oracle.encode(synth.GEOMETRY, w.vane, w.strip)
+    mism = 0
+    mp = tr.shape[1]
+    for k in ids:
+        sl = w.window(int(k))
+        r = oracle.find_window(synth.GEOMETRY, cfg["n_theta"], cfg["n_rho"], phi[sl], z[sl],
+                               max_peaks=mp)
+        pk = np.zeros((1, mp), oracle.PEAK_DTYPE)
+        pk[0, :r["n_peaks"]] = r["peaks"]
+        fr = dict(peaks=pk, n_peaks=np.array([r["n_peaks"]], np.int32),
+                  hit_track=r["hit_track"], track_hits=r["track_hits"])
+        re, rt, rh = oracle.extend(synth.GEOMETRY, phi[sl], z[sl],
+                                   np.array([0, sl.stop - sl.start], np.int64), fr, tol)
+        if (not np.array_equal(tr[int(k)][:r["n_peaks"]], re[0][:r["n_peaks"]])
+                or not np.array_equal(et[sl], rt) or not np.array_equal(eh[sl], rh)):
+            mism += 1
+    n_kept = int(npk.sum())
+    algo = 24 * w.n_hits + 12 * w.n_windows + 32 * n_kept
+    gbs = algo / (ms * 1e-3) / 1e9
+    return {"method": "seed of three hits on consecutive vanes from each peak's group, "
+                      "parabola through the last three hits extrapolated vane by vane, "
+                      f"tolerance {args.ext_tol_strips} strips",
+            "entry_point": "hough_extend (on the timed batch's hough_find output)",
+            "windows": w.n_windows, "ms_per_step": round(ms, 4),
+            "windows_per_s": round(w.n_windows / (ms * 1e-3), 1),
+            "extended_tracks": n_ext,
+            "efficiency": {"epsilon": round(eff["epsilon"], 4),
+                           "epsilon_findable": round(eff["epsilon_findable"], 4),
+                           "found": eff["found"], "all": eff["all"],
+                           "findable": eff["findable"], "windows": n_eff,
+                           "definition": "found = one extended track holds hits of the generated "
+                                         "track on 5 continuous vanes; findable = the generated "
+                                         "track's own hits have such a run"},
+            "hbm": {"achieved_gbs": round(gbs, 2), "peak_gbs": hbm_gbs,
+                    "frac": round(gbs / hbm_gbs, 4) if hbm_gbs else None,
+                    "algorithmic_bytes": algo,
+                    "bound": "latency: one warp per window, a dependent chain of vane steps"},
+            "parity_sample": {"windows": len(ids), "mismatched": mism}}
+
+
 def _coarse_fine_leg(args, dev, stream, flush, w, hits, offs):
     """The paper's own two-stage search (coarse 18 x 100, then 10 x 10 of the
     180 x 1000 grid; one line per window) on the same batch, and how often its
@@ -656,6 +733,8 @@ def run_ours(args):
             if args.coarse_fine else None
         iterative = _iterative_leg(args, dev, stream, w, hits, offs, out) \
             if args.iter_windows > 0 else None
+        extension = _extension_leg(args, dev, stream, flush, w, hits, offs, out,
+                                   peaks_meas.get("hbm_gbs")) if args.extend else None
         result = {
             "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
@@ -686,6 +765,7 @@ def run_ours(args):
             "time_slicing": slicing,
             "coarse_to_fine": coarse_fine,
             "iterative": iterative,
+            "track_extension": extension,
             "latency_us": {"p50": serving["p50_us"], "p99": serving["p99_us"],
                            "source": "serving leg"} if serving else None,
             "cpu_baseline": cpu,
@@ -745,6 +825,10 @@ def main():
     ap.add_argument("--slice-us", type=float, default=100.0)
     ap.add_argument("--no-coarse-fine", dest="coarse_fine", action="store_false")
     ap.add_argument("--iter-windows", type=int, default=20000)
+    ap.add_argument("--no-extend", dest="extend", action="store_false",
+                    help="skip the track-extension leg")
+    ap.add_argument("--ext-tol-strips", type=int, default=16)
+    ap.add_argument("--ext-eff-windows", type=int, default=5000)
     ap.add_argument("--slice-rate", type=float, default=0.6)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the library's default launch shape instead of autotuning it")

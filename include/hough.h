@@ -282,6 +282,68 @@ int hough_find_iterative(hough_ctx *ctx, const hough_hits *hits, const int64_t *
                          void *stream);
 
 /*
+ * Track extension (Section 4: three RecoHits on consecutive vanes form a
+ * seed, whose trajectory is extrapolated to neighbouring vanes forward and
+ * backward, within the time window), run on the output of hough_find for the
+ * same hits and windows.
+ *
+ * A hit takes part when hough_find did not reject it (hit_track != -2) and it
+ * lies on a vane: phi = k * vane step with 0 <= k < n_vanes (always so for
+ * strip addresses).  Vanes are neighbours modulo n_vanes.  The peaks of a
+ * window are taken in their order; a hit claimed by a track is not available
+ * to a later one.  For peak p:
+ *   seed: among the unclaimed hits a, b, c of the peak's group (track_hits)
+ *     on vanes k - 1, k, k + 1 with bend |z_a - 2 z_b + z_c| <= tol_z, the
+ *     one with the smallest (bend, b, a, c), comparing window-local indices;
+ *     none: the peak gives no track;
+ *   forward: the parabola through the last three hits predicts
+ *     z = 3 z_2 - 3 z_1 + z_0 on the next vane; the unclaimed hit of the
+ *     window on that vane nearest to it within tol_z is taken (ties: the
+ *     lower z, then the lower index); stop when there is none;
+ *   backward: the same from the seed's first hit to lower vanes;
+ *   a track holds at most n_vanes hits, one per vane.
+ * All integer, so the result is exact.
+ *
+ * Arguments (device buffers, caller-owned; window-local indices):
+ *   found          hough_find's outputs for these hits and windows: peaks,
+ *                  n_peaks, hit_track and track_hits are read;
+ *   tol_z          0..HOUGH_EXT_MAX_TOL, in z units (1/z_u_per_mm mm);
+ *   out->tracks    [n_windows * max_peaks]: entry p of window w describes
+ *                  peak p (p < n_peaks[w]): first_vane (vane of the track's
+ *                  first hit in increasing-vane order, -1 none), n_hits,
+ *                  hit_begin (offset in ext_hits), seed_mid (the seed's middle
+ *                  hit, -1 none);
+ *   out->ext_track [n_hits]: track holding the hit, -1 none;
+ *   out->ext_hits  [n_hits]: per window, the hits of track 0 in increasing
+ *                  vane order from its first vane, then track 1's, ..., then
+ *                  every unclaimed hit in increasing index;
+ *   out->window_status [n_windows]: 0, or HOUGH_WIN_TOO_LARGE for a window of
+ *                  more than HOUGH_EXT_MAX_HITS hits (no track, nothing
+ *                  claimed, ext_hits in index order).
+ * Asynchronous on stream; one or two launches.  Errors: INVALID_ARG (NULL
+ * pointer, tol_z out of range), UNSUPPORTED_SHAPE (n_vanes outside
+ * 3..HOUGH_EXT_MAX_VANES), CUDA.
+ */
+#define HOUGH_EXT_MAX_HITS 4096
+#define HOUGH_EXT_MAX_VANES 256
+#define HOUGH_EXT_MAX_TOL ((1 << 19) - 1)
+typedef struct hough_ext_track {
+    int32_t first_vane;
+    int32_t n_hits;
+    int32_t hit_begin;
+    int32_t seed_mid;
+} hough_ext_track;
+typedef struct hough_extension {
+    hough_ext_track *tracks;
+    int32_t *ext_track;
+    int32_t *ext_hits;
+    uint32_t *window_status;
+} hough_extension;
+int hough_extend(hough_ctx *ctx, const hough_hits *hits, const int64_t *window_offsets,
+                 int64_t n_windows, const hough_tracks *found, int32_t tol_z,
+                 hough_extension *out, void *stream);
+
+/*
  * Time slicing on the device (Section 5: the hits of a readout are divided
  * into overlapping time windows of 10 ns with a sliding step of 5 ns;
  * Section 6: each window is one unit of work).  Window k, 0 <= k < n_windows,

@@ -33,6 +33,8 @@ CF_DTYPE = np.dtype([(k, "<i4") for k in ("coarse_theta", "coarse_rho", "coarse_
 
 ITER_DTYPE = np.dtype([(k, "<i4") for k in ("theta", "rho", "votes", "n_hits")])
 
+EXT_DTYPE = np.dtype([(k, "<i4") for k in ("first_vane", "n_hits", "hit_begin", "seed_mid")])
+
 WIN_PEAK_OVERFLOW = 1
 WIN_HIT_OUT_OF_RANGE = 2
 WIN_VOTE_OUT_OF_RANGE = 4
@@ -93,6 +95,12 @@ def _load():
         lib.oracle_coarse_fine_batch.restype = i32
         lib.oracle_iterative_batch.argtypes = [P, i32, i32, P, P, P, P, i64, i32, P, P, P]
         lib.oracle_iterative_batch.restype = i32
+        lib.oracle_extend_window.argtypes = [P, P, P, i64, P, ctypes.c_int32, P, P,
+                                             ctypes.c_int32, P, P, P]
+        lib.oracle_extend_window.restype = i32
+        lib.oracle_extend_batch.argtypes = [P, P, P, P, i64, P, P, ctypes.c_int32, P, P,
+                                            ctypes.c_int32, P, P, P]
+        lib.oracle_extend_batch.restype = i32
         _lib = lib
     return _lib
 
@@ -293,3 +301,67 @@ def iterative(geom: dict, n_theta: int, n_rho: int, phi_q, z_q, offsets, max_tra
     if rc != 0:
         raise ValueError("oracle_iterative_batch: bad arguments")
     return tracks, n_tracks, ht[:len(phi_q)]
+
+
+def extend(geom: dict, phi_q, z_q, offsets, found: dict, tol_z: int):
+    """Track extension (Section 4) of a CSR batch, from the output of
+    find_batch on the same hits: (ext[n_windows, max_peaks] EXT_DTYPE,
+    ext_track[n_hits], ext_hits[n_hits]), per-hit arrays window-local."""
+    lib = _load()
+    g = make_geometry(geom)
+    phi_q = np.ascontiguousarray(phi_q, np.int32)
+    z_q = np.ascontiguousarray(z_q, np.int32)
+    offsets = np.ascontiguousarray(offsets, np.int64)
+    nw = len(offsets) - 1
+    pk = np.ascontiguousarray(found["peaks"])
+    max_peaks = pk.shape[1]
+    n_peaks = np.ascontiguousarray(found["n_peaks"], np.int32)
+    hit_track = np.ascontiguousarray(found["hit_track"], np.int32)
+    track_hits = np.ascontiguousarray(found["track_hits"], np.int32)
+    ext = np.zeros((nw, max(max_peaks, 1)), EXT_DTYPE)
+    n = len(phi_q)
+    ext_track = np.zeros(max(n, 1), np.int32)
+    ext_hits = np.zeros(max(n, 1), np.int32)
+    rc = lib.oracle_extend_batch(ctypes.byref(g), _ptr(phi_q), _ptr(z_q), _ptr(offsets), nw,
+                                 _ptr(pk), _ptr(n_peaks), max_peaks, _ptr(hit_track),
+                                 _ptr(track_hits), int(tol_z), _ptr(ext), _ptr(ext_track),
+                                 _ptr(ext_hits))
+    if rc != 0:
+        raise ValueError("oracle_extend_batch: bad arguments")
+    return ext[:, :max_peaks], ext_track[:n], ext_hits[:n]
+
+
+def extend_window(geom: dict, phi_q, z_q, groups, tol_z: int, rejected=()):
+    """Track extension of one window from given step-D groups: `groups` is a
+    list (in peak order) of lists of hit indices in increasing order; hits in
+    `rejected` are marked as rejected by the find step.  Returns
+    (ext[len(groups)] EXT_DTYPE, ext_track, ext_hits)."""
+    lib = _load()
+    g = make_geometry(geom)
+    phi_q = np.ascontiguousarray(phi_q, np.int32)
+    z_q = np.ascontiguousarray(z_q, np.int32)
+    n = len(phi_q)
+    pk = np.zeros(max(len(groups), 1), PEAK_DTYPE)
+    hit_track = np.full(max(n, 1), -1, np.int32)
+    hit_track[list(rejected)] = -2
+    assert not set(rejected) & {h for g_ in groups for h in g_}, "rejected hits have no group"
+    order = []
+    assert sum(len(g_) for g_ in groups) == len({h for g_ in groups for h in g_}), \
+        "step-D groups are disjoint"
+    for p, grp in enumerate(groups):
+        pk[p]["hit_begin"] = len(order)
+        pk[p]["n_hits"] = len(grp)
+        order += list(grp)
+        hit_track[list(grp)] = p
+    order += [h for h in range(n) if h not in set(order)]
+    track_hits = np.zeros(max(n, 1), np.int32)
+    track_hits[:n] = order
+    ext = np.zeros(max(len(groups), 1), EXT_DTYPE)
+    ext_track = np.zeros(max(n, 1), np.int32)
+    ext_hits = np.zeros(max(n, 1), np.int32)
+    rc = lib.oracle_extend_window(ctypes.byref(g), _ptr(phi_q), _ptr(z_q), n, _ptr(pk),
+                                  len(groups), _ptr(hit_track), _ptr(track_hits), int(tol_z),
+                                  _ptr(ext), _ptr(ext_track), _ptr(ext_hits))
+    if rc != 0:
+        raise ValueError("oracle_extend_window: bad arguments")
+    return ext[:len(groups)], ext_track[:n], ext_hits[:n]

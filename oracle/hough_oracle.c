@@ -715,3 +715,192 @@ int oracle_iterative_batch(const oracle_geometry *g, int n_theta, int n_rho,
     }
     return 0;
 }
+
+/* --------------------------------------------------------- track extension */
+
+typedef struct {
+    int32_t first_vane; /* vane of the track's first hit in increasing-vane order, -1: none */
+    int32_t n_hits;     /* hits of the track, one per vane (0: the peak gave no seed) */
+    int32_t hit_begin;  /* where the track's hits start in ext_hits */
+    int32_t seed_mid;   /* window-local index of the seed's middle hit, -1: none */
+} oracle_ext_track;
+
+static int64_t abs64(int64_t x) { return x < 0 ? -x : x; }
+
+/*
+ * Track extension of one window (Section 4: a seed of three RecoHits on
+ * consecutive vanes, its trajectory extrapolated to the neighbouring vanes
+ * forward and backward, confined to the time window).  Inputs are the
+ * window's encoded hits and the output of steps C-D for it (peaks in the
+ * canonical order with their hit groups in track_hits, hit_track per hit).
+ *
+ * A hit takes part if it was not rejected (hit_track != -2) and lies on a
+ * vane, phi_q = k * (360 deg / n_vanes) with 0 <= k < n_vanes; its vane is k.
+ * Vanes are neighbours modulo n_vanes (the vanes form a ring).  The peaks are
+ * taken in their order; a hit that a track has taken ("claimed") is not
+ * available to any later one.  For peak p:
+ *   seed: over the unclaimed hits a, b, c of the peak's group with
+ *         vane(a) = vane(b) - 1 and vane(c) = vane(b) + 1 and
+ *         |z_a - 2 z_b + z_c| <= tol_z, the one with the smallest
+ *         (|z_a - 2 z_b + z_c|, b, a, c), comparing hit indices; no such
+ *         triplet: the peak gives no track;
+ *   forward: with q0, q1, q2 the last three hits (in vane order), predict
+ *         z = 3 z_q2 - 3 z_q1 + z_q0 (the parabola through them, one vane on)
+ *         on vane(q2) + 1; take the unclaimed hit of the window on that vane
+ *         nearest the prediction within tol_z (ties: the lower z, then the
+ *         lower index); stop when there is none;
+ *   backward: the same from the seed's first hit towards lower vanes;
+ *   a track never holds more hits than there are vanes.
+ * Outputs: ext[p] for every peak, ext_track[h] = index of the track holding
+ * hit h or -1, and ext_hits: the hits of track 0 in increasing vane order
+ * from its first vane, then those of track 1, ..., then every hit that no
+ * track holds, in increasing index.  Returns 0, -1 on bad arguments.
+ */
+int oracle_extend_window(const oracle_geometry *g, const int32_t *phi_q, const int32_t *z_q,
+                         int64_t n_hits, const oracle_peak *peaks, int32_t n_peaks,
+                         const int32_t *hit_track, const int32_t *track_hits, int32_t tol_z,
+                         oracle_ext_track *ext, int32_t *ext_track, int32_t *ext_hits)
+{
+    if (!g || g->n_vanes < 3 || tol_z < 0 || n_hits < 0 || n_peaks < 0)
+        return -1;
+    const int nv = g->n_vanes;
+    const int64_t vstep = (int64_t)360 * g->phi_u_per_deg / nv;
+    int32_t *vane = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n_hits > 0 ? n_hits : 1));
+    int64_t *line = (int64_t *)malloc(sizeof(int64_t) * (size_t)(2 * nv + 4));
+    for (int64_t h = 0; h < n_hits; ++h) {
+        vane[h] = -1;
+        ext_track[h] = -1;
+        if (hit_track[h] == -2 || !hit_is_valid(g, phi_q[h], z_q[h]) || vstep <= 0)
+            continue;
+        if (phi_q[h] % vstep == 0 && phi_q[h] / vstep < nv)
+            vane[h] = (int32_t)(phi_q[h] / vstep);
+    }
+    for (int32_t p = 0; p < n_peaks; ++p) {
+        ext[p].first_vane = -1;
+        ext[p].n_hits = 0;
+        ext[p].hit_begin = 0;
+        ext[p].seed_mid = -1;
+        const int32_t *grp = track_hits + peaks[p].hit_begin;
+        const int32_t m = peaks[p].n_hits;
+        /* seed */
+        int64_t bc = -1, ba = -1, bb = -1, bcc = -1;
+        for (int32_t ib = 0; ib < m; ++ib) {
+            int32_t b = grp[ib];
+            if (vane[b] < 0 || ext_track[b] >= 0)
+                continue;
+            for (int32_t ia = 0; ia < m; ++ia) {
+                int32_t a = grp[ia];
+                if (vane[a] < 0 || ext_track[a] >= 0 || vane[a] != (vane[b] - 1 + nv) % nv)
+                    continue;
+                for (int32_t ic = 0; ic < m; ++ic) {
+                    int32_t c = grp[ic];
+                    if (vane[c] < 0 || ext_track[c] >= 0 || vane[c] != (vane[b] + 1) % nv)
+                        continue;
+                    int64_t curv = abs64((int64_t)z_q[a] - 2 * (int64_t)z_q[b] + z_q[c]);
+                    if (curv > tol_z)
+                        continue;
+                    int better = bc < 0 || curv < bc ||
+                                 (curv == bc && (b < bb || (b == bb && (a < ba ||
+                                  (a == ba && c < bcc)))));
+                    if (better) {
+                        bc = curv;
+                        ba = a;
+                        bb = b;
+                        bcc = c;
+                    }
+                }
+            }
+        }
+        if (bc < 0)
+            continue;
+        /* line[lo..hi) holds the track in increasing vane order */
+        int lo = nv + 1, hi = nv + 1;
+        line[hi++] = ba;
+        line[hi++] = bb;
+        line[hi++] = bcc;
+        ext_track[ba] = ext_track[bb] = ext_track[bcc] = p;
+        /* forward */
+        while (hi - lo < nv) {
+            int64_t q0 = line[hi - 3], q1 = line[hi - 2], q2 = line[hi - 1];
+            int tv = (vane[q2] + 1) % nv;
+            int64_t pred = 3 * (int64_t)z_q[q2] - 3 * (int64_t)z_q[q1] + z_q[q0];
+            int64_t best = -1, bd = 0;
+            for (int64_t h = 0; h < n_hits; ++h) {
+                if (vane[h] != tv || ext_track[h] >= 0)
+                    continue;
+                int64_t d = abs64((int64_t)z_q[h] - pred);
+                if (d > tol_z)
+                    continue;
+                if (best < 0 || d < bd || (d == bd && z_q[h] < z_q[best]))
+                    best = h, bd = d; /* equal d and z: the earlier index stays */
+            }
+            if (best < 0)
+                break;
+            ext_track[best] = p;
+            line[hi++] = best;
+        }
+        /* backward */
+        while (hi - lo < nv) {
+            int64_t q0 = line[lo + 2], q1 = line[lo + 1], q2 = line[lo];
+            int tv = (vane[q2] - 1 + nv) % nv;
+            int64_t pred = 3 * (int64_t)z_q[q2] - 3 * (int64_t)z_q[q1] + z_q[q0];
+            int64_t best = -1, bd = 0;
+            for (int64_t h = 0; h < n_hits; ++h) {
+                if (vane[h] != tv || ext_track[h] >= 0)
+                    continue;
+                int64_t d = abs64((int64_t)z_q[h] - pred);
+                if (d > tol_z)
+                    continue;
+                if (best < 0 || d < bd || (d == bd && z_q[h] < z_q[best]))
+                    best = h, bd = d;
+            }
+            if (best < 0)
+                break;
+            ext_track[best] = p;
+            line[--lo] = best;
+        }
+        ext[p].first_vane = vane[line[lo]];
+        ext[p].n_hits = hi - lo;
+        ext[p].seed_mid = (int32_t)bb;
+    }
+    /* ext_hits: tracks in peak order, each in increasing vane order, then the rest */
+    int32_t pos = 0;
+    for (int32_t p = 0; p < n_peaks; ++p) {
+        ext[p].hit_begin = pos;
+        for (int32_t k = 0; k < ext[p].n_hits; ++k) {
+            int tv = (ext[p].first_vane + k) % nv;
+            for (int64_t h = 0; h < n_hits; ++h)
+                if (ext_track[h] == p && vane[h] == tv)
+                    ext_hits[pos++] = (int32_t)h;
+        }
+    }
+    for (int64_t h = 0; h < n_hits; ++h)
+        if (ext_track[h] < 0)
+            ext_hits[pos++] = (int32_t)h;
+    free(line);
+    free(vane);
+    return 0;
+}
+
+/* A CSR batch of windows, each through oracle_extend_window, with the layout of
+ * oracle_find_batch (peaks and ext strided by max_peaks, per-hit arrays
+ * window-local).  Returns 0, -1 on bad arguments. */
+int oracle_extend_batch(const oracle_geometry *g, const int32_t *phi_q, const int32_t *z_q,
+                        const int64_t *offsets, int64_t n_windows, const oracle_peak *peaks,
+                        const int32_t *n_peaks, int32_t max_peaks, const int32_t *hit_track,
+                        const int32_t *track_hits, int32_t tol_z, oracle_ext_track *ext,
+                        int32_t *ext_track, int32_t *ext_hits)
+{
+    for (int64_t w = 0; w < n_windows; ++w) {
+        int64_t b = offsets[w], e = offsets[w + 1];
+        if (b < 0 || e < b || n_peaks[w] < 0 || n_peaks[w] > max_peaks)
+            return -1;
+        int rc = oracle_extend_window(g, phi_q + b, z_q + b, e - b,
+                                      peaks + (size_t)w * max_peaks, n_peaks[w], hit_track + b,
+                                      track_hits + b, tol_z, ext + (size_t)w * max_peaks,
+                                      ext_track + b, ext_hits + b);
+        if (rc != 0)
+            return rc;
+    }
+    return 0;
+}

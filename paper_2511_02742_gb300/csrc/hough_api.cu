@@ -21,6 +21,7 @@
 #include "hough_kernels.cuh"
 #include "hough_coarse_fine.cuh"
 #include "hough_iterative.cuh"
+#include "hough_extend.cuh"
 
 // Whether every valid hit votes inside [0, n_rho) in every row: the bin is
 // monotone in phi and in z, so the four corners of the detector box bound it.
@@ -713,6 +714,62 @@ int hough_find_iterative(hough_ctx *ctx, const hough_hits *hits, const int64_t *
     if (cudaGetLastError() != cudaSuccess)
         return fail(ctx, HOUGH_ERR_CUDA);
     ctx->launches += 1;
+    return HOUGH_OK;
+}
+
+int hough_extend(hough_ctx *ctx, const hough_hits *hits, const int64_t *window_offsets,
+                 int64_t n_windows, const hough_tracks *found, int32_t tol_z,
+                 hough_extension *out, void *stream)
+{
+    if (!ctx || !hits_ok(hits) || n_windows < 0 || !found || !out || tol_z < 0 ||
+        tol_z > HOUGH_EXT_MAX_TOL || n_windows >= (1ll << 31) - 65536 ||
+        (n_windows > 0 && (!window_offsets || !found->peaks || !found->n_peaks ||
+                           !out->tracks || !out->window_status)) ||
+        (hits->n_hits > 0 && (!found->hit_track || !found->track_hits || !out->ext_track ||
+                              !out->ext_hits)))
+        return fail(ctx, HOUGH_ERR_INVALID_ARG);
+    const int nv = ctx->g.n_vanes;
+    if (nv < 3 || nv > HOUGH_EXT_MAX_VANES || 360LL * ctx->g.phi_u_per_deg / nv <= 0)
+        return fail(ctx, HOUGH_ERR_UNSUPPORTED_SHAPE);
+    if (n_windows == 0)
+        return HOUGH_OK;
+    hough_launch l{32, 32, 0, 1};
+    hk::ExtParams q{};
+    hough_tracks f = *found;
+    f.window_status = nullptr;
+    f.acc = nullptr;
+    q.k = make_params(ctx, hits, window_offsets, n_windows, &f, nullptr, l);
+    q.n_vanes = nv;
+    q.tol_z = tol_z;
+    q.ext = reinterpret_cast<int4 *>(out->tracks);
+    q.ext_track = out->ext_track;
+    q.ext_hits = out->ext_hits;
+    q.status = out->window_status;
+    // a small stage for most windows (many warps per SM), then the large one
+    // for the windows above it
+    const int caps[2] = {1024, HOUGH_EXT_MAX_HITS};
+    long long lo = -1;
+    for (int pass = 0; pass < 2; ++pass) {
+        const size_t smem = hk::ext_smem_bytes(caps[pass], nv);
+        if (smem > ctx->smem_optin)
+            return fail(ctx, HOUGH_ERR_UNSUPPORTED_SHAPE);
+        if (cudaFuncSetAttribute(hk::extend_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess)
+            return fail(ctx, HOUGH_ERR_CUDA);
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hk::extend_kernel, 32, smem) !=
+                cudaSuccess || occ < 1)
+            return fail(ctx, HOUGH_ERR_CUDA);
+        q.cap = caps[pass];
+        q.lo = lo;
+        q.flag_large = pass == 1;
+        const long long grid = std::min<long long>(n_windows, (long long)ctx->num_sms * occ);
+        hk::extend_kernel<<<(unsigned)grid, 32, smem, (cudaStream_t)stream>>>(q);
+        if (cudaGetLastError() != cudaSuccess)
+            return fail(ctx, HOUGH_ERR_CUDA);
+        ctx->launches += 1;
+        lo = caps[pass];
+    }
     return HOUGH_OK;
 }
 

@@ -28,6 +28,9 @@ HOUGH_WIN_VOTE_OUT_OF_RANGE = 4
 HOUGH_WIN_BAD_OFFSETS = 8
 HOUGH_WIN_TOO_LARGE = 16
 HOUGH_ITER_MAX_HITS = 4096
+HOUGH_EXT_MAX_HITS = 4096
+HOUGH_EXT_MAX_VANES = 256
+HOUGH_EXT_MAX_TOL = (1 << 19) - 1
 HOUGH_FLAG_EXPORT_ACC = 1
 HOUGH_ERR_TIMEOUT = -4
 HOUGH_ERR_UNSUPPORTED_SHAPE = -5
@@ -145,6 +148,7 @@ def load(build_if_missing: bool = False):
         "hough_find_coarse_fine": ([P, P, P, i64, P, P, P], i32),
         "hough_find_iterative": ([P, P, P, i64, ctypes.c_int32, P, P, P, P, P], i32),
         "hough_time_slice": ([P, P, P, P, i64, i64, i64, i64, i64, P, P, P, i64, P, P, P], i32),
+        "hough_extend": ([P, P, P, i64, P, ctypes.c_int32, P, P], i32),
         "hough_server_create": ([P, P, P], i32),
         "hough_server_submit": ([P, P, P], i32),
         "hough_server_wait": ([P, ctypes.c_uint64, i64, P], i32),
@@ -269,6 +273,24 @@ def hough_find_iterative(ctx, hits: hough_hits, window_offsets, n_windows: int, 
                                        max_tracks, _ptr(tracks), _ptr(n_tracks), _ptr(hit_track),
                                        _ptr(window_status), _stream(stream)),
            "hough_find_iterative")
+
+
+EXT_DTYPE = np.dtype([(k, "<i4") for k in ("first_vane", "n_hits", "hit_begin", "seed_mid")])
+
+
+class hough_extension(ctypes.Structure):
+    _fields_ = [("tracks", P), ("ext_track", P), ("ext_hits", P), ("window_status", P)]
+
+
+def hough_extend(ctx, hits: hough_hits, window_offsets, n_windows: int, found: hough_tracks,
+                 tol_z: int, out: dict, stream=None) -> None:
+    """Track extension on hough_find's outputs; out: dict of device tensors
+    tracks [n_windows, max_peaks, 4], ext_track, ext_hits, window_status."""
+    ext = hough_extension(_ptr(out["tracks"]), _ptr(out["ext_track"]), _ptr(out["ext_hits"]),
+                          _ptr(out["window_status"]))
+    _check(load().hough_extend(ctx, ctypes.byref(hits), _ptr(window_offsets), int(n_windows),
+                               ctypes.byref(found), int(tol_z), ctypes.byref(ext),
+                               _stream(stream)), "hough_extend")
 
 
 def hough_time_slice(ctx, t, in0, in1, t0: int, step: int, length: int, n_windows: int,
@@ -426,6 +448,24 @@ class Finder:
         if out is None:
             out = self.alloc_outputs(n_windows, hs.n_hits, device="cpu")
         hough_find_host(self.ctx, hs, offsets, n_windows, make_tracks(out), stream)
+        return out
+
+    def extend(self, hits: dict, offsets, found: dict, tol_z: int, out: dict | None = None,
+               stream=None) -> dict:
+        """Track extension (hough_extend) on the outputs of find() for the same
+        hits and windows; returns dict(tracks, ext_track, ext_hits, window_status)."""
+        import torch
+        n_windows = int(offsets.numel()) - 1
+        hs = self.hits_struct(hits)
+        if out is None:
+            dev = found["n_peaks"].device
+            out = dict(
+                tracks=torch.zeros((n_windows, max(self.max_peaks, 1), 4), dtype=torch.int32,
+                                   device=dev),
+                ext_track=torch.zeros(max(hs.n_hits, 1), dtype=torch.int32, device=dev),
+                ext_hits=torch.zeros(max(hs.n_hits, 1), dtype=torch.int32, device=dev),
+                window_status=torch.zeros(max(n_windows, 1), dtype=torch.int32, device=dev))
+        hough_extend(self.ctx, hs, offsets, n_windows, make_tracks(found), tol_z, out, stream)
         return out
 
     def plan(self, hits: dict, offsets, out: dict, stream=None):

@@ -13,7 +13,10 @@ from parity_helpers import G, assert_window_equal, to_numpy
 pytestmark = pytest.mark.gpu
 
 
-def _run_planned(hough, w, n_theta, n_rho, export=False, tune_windows=20000):
+TOL_Z = 16 * 38
+
+
+def _run_planned(hough, w, n_theta, n_rho, export=False, tune_windows=20000, extend=False):
     import torch
     f = hough.Finder(n_theta, n_rho, export_acc=export)
     hits = dict(vane=torch.from_numpy(w.vane).cuda(), strip=torch.from_numpy(w.strip).cuda())
@@ -29,6 +32,9 @@ def _run_planned(hough, w, n_theta, n_rho, export=False, tune_windows=20000):
     torch.cuda.synchronize()
     hough.hough_plan_destroy(plan)
     launch = hough.hough_get_launch(f.ctx)
+    if extend:
+        out["ext"] = f.extend(hits, offs, out, TOL_Z)
+        torch.cuda.synchronize()
     f.close()
     return out, launch
 
@@ -37,12 +43,23 @@ def test_batched_full_size_sampled(hough):
     cfg = synth.WORKLOADS["batched"]
     w = synth.workload("batched")
     assert w.n_windows == 100000
-    out, launch = _run_planned(hough, w, cfg["n_theta"], cfg["n_rho"])
+    out, launch = _run_planned(hough, w, cfg["n_theta"], cfg["n_rho"], extend=True)
+    ext = out.pop("ext")
     g = to_numpy(out, w.n_hits)
     ids = np.random.default_rng(2).choice(w.n_windows, 60, replace=False)
     refs = oracle_windows(w, ids, cfg["n_theta"], cfg["n_rho"])
+    from paper_2511_02742_gb300 import hough as hb
+    et = ext["tracks"].cpu().numpy().view(hb.EXT_DTYPE).reshape(w.n_windows, -1)
+    ex_track = ext["ext_track"].cpu().numpy()
+    ex_hits = ext["ext_hits"].cpu().numpy()
+    assert (ext["window_status"].cpu().numpy()[:w.n_windows] == 0).all()
     for k, r in zip(ids, refs):
-        assert_window_equal(g, int(k), r, w.window(int(k)), check_acc=False)
+        sl = w.window(int(k))
+        assert_window_equal(g, int(k), r, sl, check_acc=False)
+        re, rt, rh = oracle_extend_window(w, int(k), r)
+        np.testing.assert_array_equal(et[int(k)][:r["n_peaks"]], re[0][:r["n_peaks"]])
+        np.testing.assert_array_equal(ex_track[sl], rt)
+        np.testing.assert_array_equal(ex_hits[sl], rh)
 
 
 def test_high_pileup_full_size_sampled_with_accumulators(hough):
@@ -67,3 +84,14 @@ def oracle_windows(w, ids, n_theta, n_rho, export=False):
         sl = w.window(int(k))
         res.append(oracle.find_window(G, n_theta, n_rho, phi[sl], z[sl]))
     return res
+
+
+def oracle_extend_window(w, k, r, max_peaks=64):
+    """The oracle's track extension of window k from its own step A-D result r."""
+    sl = w.window(k)
+    phi, z = oracle.encode(G, w.vane[sl], w.strip[sl])
+    pk = np.zeros((1, max_peaks), oracle.PEAK_DTYPE)
+    pk[0, :r["n_peaks"]] = r["peaks"]
+    found = dict(peaks=pk, n_peaks=np.array([r["n_peaks"]], np.int32), hit_track=r["hit_track"],
+                 track_hits=r["track_hits"])
+    return oracle.extend(G, phi, z, np.array([0, sl.stop - sl.start], np.int64), found, TOL_Z)

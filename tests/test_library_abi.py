@@ -101,6 +101,7 @@ def test_null_pointers_are_rejected(lib):
     assert lib.hough_encode(None, None, None, 0, None, None, None) == -1
     assert lib.hough_find_coarse_fine(None, None, None, 0, None, None, None) == -1
     assert lib.hough_find_iterative(None, None, None, 0, 1, None, None, None, None, None) == -1
+    assert lib.hough_extend(None, None, None, 0, None, 0, None, None) == -1
     assert lib.hough_time_slice(None, None, None, None, 0, 0, 5, 10, 1, None, None, None, 0,
                                 None, None, None) == -1
     assert lib.hough_plan_create(None, None, None, 0, None, None, None) == -1
@@ -137,7 +138,7 @@ def test_binding_structs_match_the_header(tmp_path):
     from paper_2511_02742_gb300 import hough
     structs = [hough.hough_geometry, hough.hough_thresholds, hough.hough_hits, hough.hough_tracks,
                hough.hough_launch, hough.hough_server_config, hough.hough_request,
-               hough.hough_request_result, hough.hough_server_stats]
+               hough.hough_request_result, hough.hough_server_stats, hough.hough_extension]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hough.h"', 'int main(void) {']
     for st in structs:
         n = st.__name__
@@ -145,6 +146,7 @@ def test_binding_structs_match_the_header(tmp_path):
         for field, _ in st._fields_:
             lines.append(f'printf("{n} {field} %zu\\n", offsetof({n}, {field}));')
     lines.append('printf("hough_peak size %zu\\n", sizeof(hough_peak));')
+    lines.append('printf("hough_ext_track size %zu\\n", sizeof(hough_ext_track));')
     lines += ['return 0;', '}']
     src = tmp_path / "layout.c"
     src.write_text("\n".join(lines))
@@ -159,3 +161,4 @@ def test_binding_structs_match_the_header(tmp_path):
         for field, _ in st._fields_:
             assert int(got[f"{n} {field}"]) == getattr(st, field).offset, (n, field)
     assert int(got["hough_peak size"]) == hough.PEAK_DTYPE.itemsize == 16
+    assert int(got["hough_ext_track size"]) == hough.EXT_DTYPE.itemsize == 16
