@@ -118,22 +118,27 @@ def test_second_track_keeps_its_own_hits():
     assert ext[1]["hit_begin"] == 8
 
 
-def test_extension_wraps_around_the_ring_of_vanes():
-    vanes = [37, 38, 39, 0, 1, 2]
-    strips = [200 + 5 * k for k in range(6)]
-    ext, ext_track, ext_hits = run(vanes, strips, [[1, 2, 3]])
-    assert ext[0]["n_hits"] == 6 and ext[0]["first_vane"] == 37
-    assert list(ext_hits) == [0, 1, 2, 3, 4, 5]
+@pytest.mark.parametrize("seed", [[1, 2, 3], [0, 1, 2], [4, 5, 6]])
+def test_extension_wraps_around_the_ring_of_vanes(seed):
+    """A line over vanes 37..39, 0..3: seeded across the joint, before it
+    (forward crosses 39 -> 0) and after it (backward crosses 0 -> 39)."""
+    vanes = [37, 38, 39, 0, 1, 2, 3]
+    strips = [200 + 5 * k for k in range(7)]
+    ext, ext_track, ext_hits = run(vanes, strips, [seed])
+    assert ext[0]["n_hits"] == 7 and ext[0]["first_vane"] == 37
+    assert list(ext_hits) == list(range(7))
 
 
 def test_a_track_never_exceeds_the_number_of_vanes():
-    """A flat line on all 40 vanes: the seed with the lowest middle index is
-    (39, 0, 1); forward reaches vane 38 and the ring is full."""
-    vanes = list(range(40))
-    strips = [700] * 40
+    """A flat line on all 40 vanes plus a second hit on vane 39: the seed with
+    the lowest middle index is (39, 0, 1); forward reaches vane 38, the ring is
+    full and the second hit on vane 39 stays free."""
+    vanes = list(range(40)) + [39]
+    strips = [700] * 41
     ext, ext_track, ext_hits = run(vanes, strips, [list(range(40))])
     assert ext[0]["n_hits"] == 40 and ext[0]["first_vane"] == 39 and ext[0]["seed_mid"] == 0
-    assert list(ext_hits) == [39] + list(range(39))
+    assert list(ext_hits) == [39] + list(range(39)) + [40]
+    assert ext_track[40] == -1
 
 
 def test_seed_is_the_straightest_triplet_then_the_lowest_indices():
