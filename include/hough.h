@@ -320,7 +320,7 @@ int hough_find_iterative(hough_ctx *ctx, const hough_hits *hits, const int64_t *
  *   out->window_status [n_windows]: 0, or HOUGH_WIN_TOO_LARGE for a window of
  *                  more than HOUGH_EXT_MAX_HITS hits (no track, nothing
  *                  claimed, ext_hits in index order).
- * Asynchronous on stream; one or two launches.  Errors: INVALID_ARG (NULL
+ * Asynchronous on stream; three launches.  Errors: INVALID_ARG (NULL
  * pointer, tol_z out of range), UNSUPPORTED_SHAPE (n_vanes outside
  * 3..HOUGH_EXT_MAX_VANES), CUDA.
  */

@@ -745,11 +745,11 @@ int hough_extend(hough_ctx *ctx, const hough_hits *hits, const int64_t *window_o
     q.ext_track = out->ext_track;
     q.ext_hits = out->ext_hits;
     q.status = out->window_status;
-    // a small stage for most windows (many warps per SM), then the large one
-    // for the windows above it
-    const int caps[2] = {1024, HOUGH_EXT_MAX_HITS};
+    // small stages for most windows (many warps per SM), then larger ones for
+    // the windows above them
+    const int caps[3] = {512, 1536, HOUGH_EXT_MAX_HITS};
     long long lo = -1;
-    for (int pass = 0; pass < 2; ++pass) {
+    for (int pass = 0; pass < 3; ++pass) {
         const size_t smem = hk::ext_smem_bytes(caps[pass], nv);
         if (smem > ctx->smem_optin)
             return fail(ctx, HOUGH_ERR_UNSUPPORTED_SHAPE);
@@ -762,7 +762,7 @@ int hough_extend(hough_ctx *ctx, const hough_hits *hits, const int64_t *window_o
             return fail(ctx, HOUGH_ERR_CUDA);
         q.cap = caps[pass];
         q.lo = lo;
-        q.flag_large = pass == 1;
+        q.flag_large = pass == 2;
         const long long grid = std::min<long long>(n_windows, (long long)ctx->num_sms * occ);
         hk::extend_kernel<<<(unsigned)grid, 32, smem, (cudaStream_t)stream>>>(q);
         if (cudaGetLastError() != cudaSuccess)

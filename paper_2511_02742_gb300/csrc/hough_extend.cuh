@@ -166,10 +166,15 @@ __global__ void __launch_bounds__(32) extend_kernel(ExtParams q)
         int pos = 0;
         for (int pi = 0; pi < np; ++pi) {
             const int hb = pk[pi].hit_begin, m = pk[pi].n_hits;
-            const bool grp_ok = hb >= 0 && m >= 0 && (long long)hb + m <= H;
+            const bool grp_ok = hb >= 0 && m >= 3 && (long long)hb + m <= H;
+            if (!grp_ok) {                  // fewer than three hits: no seed
+                if (lane == 0)
+                    ext[pi] = make_int4(-1, 0, pos, -1);
+                continue;
+            }
             // seed: the smallest (bend, b, a, c) over the group's unclaimed triplets
             unsigned long long best = ~0ull;
-            for (int j = lane; grp_ok && j < m; j += 32) {
+            for (int j = lane; j < m; j += 32) {
                 const int b = p.track_hits[beg + hb + j];
                 if ((unsigned)b >= (unsigned)H || tag[b] != pi)
                     continue;

@@ -77,12 +77,17 @@ def test_uneven_windows_with_empty_ones(hough):
     _check(hough, w, 512, 512)
 
 
-def test_high_pileup_takes_both_launches(hough):
-    """Windows up to 1024 hits go to the first launch, larger ones to the
-    second: both kinds are present and both are exact."""
-    w = synth.workload("high_pileup", n_windows=24, seed=53)
+def test_windows_of_every_launch_tier(hough):
+    """Windows up to 512 hits go to the first launch, up to 1536 to the
+    second, up to 4096 to the third: all three kinds are present, interleaved,
+    and all are exact."""
+    w = synth.concat([synth.workload("high_pileup", n_windows=12, seed=53),
+                      synth.generate(6, ("poisson", 10, 1, 40), (100.0, 300.0), 0.02, seed=61),
+                      synth.generate(2, 110, (100.0, 300.0), 0.05, seed=62)])
+    w = w.subset(np.random.default_rng(63).permutation(w.n_windows))
     n = np.diff(w.offsets)
-    assert (n <= 1024).any() and (n > 1024).any(), n
+    assert (n <= 512).any() and ((n > 512) & (n <= 1536)).any(), n
+    assert ((n > 1536) & (n <= 4096)).any(), n
     _check(hough, w, 1024, 1024, max_peaks=256)
 
 
