@@ -319,7 +319,9 @@ int hough_find_iterative(hough_ctx *ctx, const hough_hits *hits, const int64_t *
  *                  every unclaimed hit in increasing index;
  *   out->window_status [n_windows]: 0, or HOUGH_WIN_TOO_LARGE for a window of
  *                  more than HOUGH_EXT_MAX_HITS hits (no track, nothing
- *                  claimed, ext_hits in index order).
+ *                  claimed, ext_hits in index order), or HOUGH_WIN_BAD_OFFSETS
+ *                  when the window's offsets are out of order or beyond
+ *                  n_hits (its outputs are not written).
  * Asynchronous on stream; three launches.  Errors: INVALID_ARG (NULL
  * pointer, tol_z out of range), UNSUPPORTED_SHAPE (n_vanes outside
  * 3..HOUGH_EXT_MAX_VANES), CUDA.

@@ -80,8 +80,13 @@ __global__ void __launch_bounds__(32) extend_kernel(ExtParams q)
     const int vstep = p.vane_step;
 
     for (long long w = blockIdx.x; w < p.n_windows; w += gridDim.x) {
-        const long long beg = p.offsets[w];
-        const long long n = p.offsets[w + 1] - beg;
+        const long long beg = p.offsets[w], end = p.offsets[w + 1];
+        if (!(beg >= 0 && beg <= end && end <= p.n_hits)) {
+            if (q.lo < 0 && lane == 0)      // flagged once, by the first launch
+                q.status[w] = HOUGH_WIN_BAD_OFFSETS;
+            continue;
+        }
+        const long long n = end - beg;
         if (n <= q.lo)
             continue;                       // an earlier launch took it
         const int np = min(max(p.n_peaks[w], 0), p.max_peaks);

@@ -154,3 +154,30 @@ def test_efficiency_is_the_same_from_either_side(hough):
     a = evaluate.efficiency(w.vane, w.track, w.offsets, w.track_offsets, gt)
     b = evaluate.efficiency(w.vane, w.track, w.offsets, w.track_offsets, rt)
     assert a == b and a["epsilon_findable"] > 0.6
+
+
+def test_bad_offsets_are_flagged_not_read(hough):
+    """Windows whose offsets run backwards or past the hits get
+    HOUGH_WIN_BAD_OFFSETS; the valid windows around them are exact."""
+    import torch
+    w = synth.generate(6, 5, (100.0, 300.0), 0.01, seed=64)
+    f = hough.Finder(512, 512)
+    hits = dict(vane=torch.from_numpy(w.vane).cuda(), strip=torch.from_numpy(w.strip).cuda())
+    good = torch.from_numpy(w.offsets).cuda()
+    found = f.find(hits, good)
+    bad = w.offsets.copy()
+    bad = np.concatenate([bad, [bad[-1] + 1000, bad[2]]])      # past n_hits, then backwards
+    offs = torch.from_numpy(bad).cuda()
+    nw = len(bad) - 1
+    fb = f.alloc_outputs(nw, w.n_hits)
+    f.find(hits, offs, out=fb)
+    ext = f.extend(hits, offs, fb, TOL)
+    ref = f.extend(hits, good, found, TOL)
+    torch.cuda.synchronize()
+    st = ext["window_status"].cpu().numpy()[:nw]
+    assert list(st[w.n_windows:]) == [hough.HOUGH_WIN_BAD_OFFSETS] * 2
+    assert (st[:w.n_windows] == 0).all()
+    n = w.n_hits
+    np.testing.assert_array_equal(ext["ext_track"].cpu().numpy()[:n], ref["ext_track"].cpu().numpy()[:n])
+    np.testing.assert_array_equal(ext["ext_hits"].cpu().numpy()[:n], ref["ext_hits"].cpu().numpy()[:n])
+    f.close()
