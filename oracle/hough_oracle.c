@@ -31,9 +31,9 @@
  * Two variants of steps C-D: the paper's coarse-to-fine search for one line
  * (oracle_coarse_fine_*) and the iterative highest-bin search
  * (oracle_iterative_*).
- * The readings of the points the paper leaves open (units, theta sampling,
- * fixed-point tables, threshold, tie-break, tolerance) are listed in the
- * design notes of the repository.
+ * Where the paper leaves a point open (units, theta sampling, fixed-point
+ * tables, threshold, tie-break, tolerance), the reading taken is stated at
+ * the step that uses it.
  *
  * Parity pins: tests/test_oracle_pins.py checks this file against brute force
  * on hand-built cases, the single-line closed form, the helix closed form,

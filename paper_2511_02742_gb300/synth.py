@@ -7,7 +7,7 @@ It contains none of the track-finding arithmetic (no Hough transform, no
 binning, no peak or association logic): both the CUDA path and the CPU oracle
 consume its output, and each encodes and processes it with its own code.
 
-Physics model (choices recorded in the design doc):
+Physics model:
   * detector geometry of Section 2: 40 radial vanes, z sensitive range
     +-194.56 mm (4 Z-sensors x 512 strips at 0.19 mm), radial sensitive range
     70-290 mm split into two R-sensor rows [70, 167.28] and [192.72, 290];
