@@ -268,6 +268,49 @@ def _extension_leg(args, dev, stream, flush, w, hits, offs, out_find, hbm_gbs):
             "parity_sample": {"windows": len(ids), "mismatched": mism}}
 
 
+def _fp64_leg(args, dev, stream, w, hits, offs, out_find):
+    """The FP64 variant of the find (bins from Eq. (1) in double precision) on
+    the first --fp64-windows windows: its time, and how often its top peak
+    lies within one bin of a fixed-point peak holding at least the
+    fixed-point top count minus one (windows whose top has >= 10 votes)."""
+    import torch
+    from paper_2511_02742_gb300 import hough, synth
+    cfg = synth.WORKLOADS[args.workload]
+    n = min(w.n_windows, args.fp64_windows)
+    f = hough.Finder(cfg["n_theta"], cfg["n_rho"], fp64=True)
+    out = f.alloc_outputs(n, w.n_hits)
+    f.find(hits, offs[:n + 1], out=out, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    f.find(hits, offs[:n + 1], out=out, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    f.close()
+    pa_all = hough.decode_peaks(out_find["peaks"])
+    npa = out_find["n_peaks"].cpu().numpy()
+    pb_all = hough.decode_peaks(out["peaks"])
+    npb = out["n_peaks"].cpu().numpy()
+    cmp = agree = same = 0
+    for k in range(n):
+        if npa[k] == 0 or npb[k] == 0 or pa_all[k][0]["votes"] < 10:
+            continue
+        cmp += 1
+        pa = pa_all[k][:npa[k]]
+        pb = pb_all[k][0]
+        near = pa[pa["votes"] >= int(pa[0]["votes"]) - 1]
+        ok = (np.abs(near["theta"].astype(int) - int(pb["theta"])) <= 1) & \
+             (np.abs(near["rho"].astype(int) - int(pb["rho"])) <= 1)
+        agree += bool(ok.any())
+        same += bool(pa[0]["theta"] == pb["theta"] and pa[0]["rho"] == pb["rho"])
+    return {"method": "bins from Eq. (1) in double precision (HOUGH_FLAG_FP64), same kernel otherwise",
+            "windows": n, "ms": round(ms, 3), "windows_per_s": round(n / (ms * 1e-3), 1),
+            "compared_windows": cmp,
+            "top_peak_within_one_bin": round(agree / max(cmp, 1), 4),
+            "top_peak_same_bin": round(same / max(cmp, 1), 4)}
+
+
 def _coarse_fine_leg(args, dev, stream, flush, w, hits, offs):
     """The paper's own two-stage search (coarse 18 x 100, then 10 x 10 of the
     180 x 1000 grid; one line per window) on the same batch, and how often its
@@ -737,6 +780,7 @@ def run_ours(args):
             if args.iter_windows > 0 else None
         extension = _extension_leg(args, dev, stream, flush, w, hits, offs, out,
                                    peaks_meas.get("hbm_gbs")) if args.extend else None
+        fp64 = _fp64_leg(args, dev, stream, w, hits, offs, out) if args.fp64_windows > 0 else None
         result = {
             "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
@@ -768,6 +812,7 @@ def run_ours(args):
             "coarse_to_fine": coarse_fine,
             "iterative": iterative,
             "track_extension": extension,
+            "fp64_variant": fp64,
             "latency_us": {"p50": serving["p50_us"], "p99": serving["p99_us"],
                            "source": "serving leg"} if serving else None,
             "cpu_baseline": cpu,
@@ -831,6 +876,8 @@ def main():
                     help="skip the track-extension leg")
     ap.add_argument("--ext-tol-strips", type=int, default=16)
     ap.add_argument("--ext-eff-windows", type=int, default=5000)
+    ap.add_argument("--fp64-windows", type=int, default=20000,
+                    help="windows for the FP64-variant leg (0: skip)")
     ap.add_argument("--slice-rate", type=float, default=0.6)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the library's default launch shape instead of autotuning it")

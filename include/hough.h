@@ -62,6 +62,19 @@ typedef enum hough_status {
 
 /* hough_thresholds.flags */
 #define HOUGH_FLAG_EXPORT_ACC 1u /* write the full int32 accumulator (tracks_out->acc) */
+/*
+ * FP64 variant of the find (hough_find and its host, plan and server forms):
+ * each hit's bin in a theta row comes from Eq. (1) in double precision with
+ * the Section 5 binning instead of the fixed-point tables,
+ *   b = floor(((phi/phi_u_per_deg) cos(theta_t) + (z/z_u_per_mm) sin(theta_t)
+ *              - rho_min) / ((rho_max - rho_min) / n_rho)),
+ * every operation rounded to nearest in that order (no fused multiply-add),
+ * cos and sin computed on the host in double.  Everything else (peaks,
+ * association, outputs) is unchanged.  It exists to check that the
+ * fixed-point result agrees with the continuous one within one bin; it is
+ * slower.  Not accepted by hough_find_noalloc.
+ */
+#define HOUGH_FLAG_FP64 2u
 
 /*
  * Detector geometry and fixed-point units (Section 2).  Defaults for the

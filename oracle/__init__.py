@@ -35,6 +35,7 @@ ITER_DTYPE = np.dtype([(k, "<i4") for k in ("theta", "rho", "votes", "n_hits")])
 
 EXT_DTYPE = np.dtype([(k, "<i4") for k in ("first_vane", "n_hits", "hit_begin", "seed_mid")])
 
+FLAG_FP64 = 2
 WIN_PEAK_OVERFLOW = 1
 WIN_HIT_OUT_OF_RANGE = 2
 WIN_VOTE_OUT_OF_RANGE = 4
@@ -190,11 +191,12 @@ def peaks(acc, threshold: int, max_peaks: int):
 
 
 def find_window(geom: dict, n_theta: int, n_rho: int, phi_q, z_q, vote_threshold=5,
-                assoc_tol_bins=1, max_peaks=64):
-    """One window through voting, peaks and association; returns a dict."""
+                assoc_tol_bins=1, max_peaks=64, fp64=False):
+    """One window through voting, peaks and association; returns a dict.
+    fp64: bins from Eq. (1) in double precision instead of the tables."""
     lib = _load()
     g = make_geometry(geom)
-    th = make_thresholds(vote_threshold, assoc_tol_bins, max_peaks)
+    th = make_thresholds(vote_threshold, assoc_tol_bins, max_peaks, FLAG_FP64 if fp64 else 0)
     phi_q = np.ascontiguousarray(phi_q, np.int32)
     z_q = np.ascontiguousarray(z_q, np.int32)
     n = len(phi_q)
@@ -218,11 +220,12 @@ def find_window(geom: dict, n_theta: int, n_rho: int, phi_q, z_q, vote_threshold
 
 
 def find_batch(geom: dict, n_theta: int, n_rho: int, phi_q, z_q, offsets, vote_threshold=5,
-               assoc_tol_bins=1, max_peaks=64, export_acc=False):
-    """A CSR batch of windows; outputs in the library's layout (dict of arrays)."""
+               assoc_tol_bins=1, max_peaks=64, export_acc=False, fp64=False):
+    """A CSR batch of windows; outputs in the library's layout (dict of arrays).
+    fp64: bins from Eq. (1) in double precision instead of the tables."""
     lib = _load()
     g = make_geometry(geom)
-    th = make_thresholds(vote_threshold, assoc_tol_bins, max_peaks)
+    th = make_thresholds(vote_threshold, assoc_tol_bins, max_peaks, FLAG_FP64 if fp64 else 0)
     phi_q = np.ascontiguousarray(phi_q, np.int32)
     z_q = np.ascontiguousarray(z_q, np.int32)
     offsets = np.ascontiguousarray(offsets, np.int64)

@@ -76,6 +76,10 @@ typedef struct {
 } oracle_peak;
 
 enum {
+    ORACLE_FLAG_FP64 = 2u, /* thresholds.flags: bins from Eq. (1) in double precision */
+};
+
+enum {
     ORACLE_WIN_PEAK_OVERFLOW = 1u,
     ORACLE_WIN_HIT_OUT_OF_RANGE = 2u,
     ORACLE_WIN_VOTE_OUT_OF_RANGE = 4u,
@@ -219,19 +223,23 @@ int64_t oracle_vote(const oracle_geometry *g, int n_theta, int n_rho, const int3
 /* FP64 continuous variant of step B: the bin from Eq. (1) in double precision,
  * b = floor((phi_deg*cos(theta) + z_mm*sin(theta) - rho_min) / drho).  Used to
  * check that the fixed-point bins agree within one bin.  bins[h*n_theta + t]. */
+static int64_t bin_fp64(const oracle_geometry *g, int n_theta, int n_rho, int32_t phi_q,
+                        int32_t z_q, int t)
+{
+    double drho = (g->rho_max - g->rho_min) / (double)n_rho;
+    double phi = (double)phi_q / (double)g->phi_u_per_deg;
+    double z = (double)z_q / (double)g->z_u_per_mm;
+    double theta = ((double)t + 0.5) * (M_PI / (double)n_theta);
+    double rho = phi * cos(theta) + z * sin(theta);
+    return (int64_t)floor((rho - g->rho_min) / drho);
+}
+
 void oracle_bins_fp64(const oracle_geometry *g, int n_theta, int n_rho, const int32_t *phi_q,
                       const int32_t *z_q, int64_t n_hits, int64_t *bins)
 {
-    double drho = (g->rho_max - g->rho_min) / (double)n_rho;
-    for (int64_t h = 0; h < n_hits; ++h) {
-        double phi = (double)phi_q[h] / (double)g->phi_u_per_deg;
-        double z = (double)z_q[h] / (double)g->z_u_per_mm;
-        for (int t = 0; t < n_theta; ++t) {
-            double theta = ((double)t + 0.5) * (M_PI / (double)n_theta);
-            double rho = phi * cos(theta) + z * sin(theta);
-            bins[h * n_theta + t] = (int64_t)floor((rho - g->rho_min) / drho);
-        }
-    }
+    for (int64_t h = 0; h < n_hits; ++h)
+        for (int t = 0; t < n_theta; ++t)
+            bins[h * n_theta + t] = bin_fp64(g, n_theta, n_rho, phi_q[h], z_q[h], t);
 }
 
 /* Fixed-point bins for every (hit, theta); same layout as oracle_bins_fp64. */
@@ -359,8 +367,25 @@ int oracle_find_window(const oracle_geometry *g, int n_theta, int n_rho,
     if (!acc)
         acc = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_theta * (size_t)n_rho);
 
-    /* B: vote */
-    int64_t dropped = oracle_vote(g, n_theta, n_rho, phi_q, z_q, n_hits, acc);
+    /* B: vote (the FP64 variant takes each bin from Eq. (1) in double precision) */
+    const int fp64 = (th->flags & ORACLE_FLAG_FP64) != 0;
+    int64_t dropped = 0;
+    if (!fp64) {
+        dropped = oracle_vote(g, n_theta, n_rho, phi_q, z_q, n_hits, acc);
+    } else {
+        memset(acc, 0, sizeof(int32_t) * (size_t)n_theta * (size_t)n_rho);
+        for (int64_t h = 0; h < n_hits; ++h) {
+            if (!hit_is_valid(g, phi_q[h], z_q[h]))
+                continue;
+            for (int t = 0; t < n_theta; ++t) {
+                int64_t b = bin_fp64(g, n_theta, n_rho, phi_q[h], z_q[h], t);
+                if (b >= 0 && b < n_rho)
+                    acc[(size_t)t * n_rho + (size_t)b] += 1;
+                else
+                    ++dropped;
+            }
+        }
+    }
     for (int64_t h = 0; h < n_hits; ++h)
         if (!hit_is_valid(g, phi_q[h], z_q[h]))
             st |= ORACLE_WIN_HIT_OUT_OF_RANGE;
@@ -387,7 +412,8 @@ int oracle_find_window(const oracle_geometry *g, int n_theta, int n_rho,
         hit_track[h] = -1;
         for (int32_t p = 0; p < kept; ++p) {
             int t = peaks[p].theta;
-            int64_t bh = rho_bin(phi_q[h], z_q[h], C[t], S[t], D, k);
+            int64_t bh = fp64 ? bin_fp64(g, n_theta, n_rho, phi_q[h], z_q[h], t)
+                              : rho_bin(phi_q[h], z_q[h], C[t], S[t], D, k);
             int64_t diff = bh - (int64_t)peaks[p].rho;
             if (diff < 0)
                 diff = -diff;

@@ -223,6 +223,13 @@ hk::KParams make_params(const hough_ctx *ctx, const hough_hits *hits, const int6
     p.D = (int)ctx->D;
     p.K = ctx->K;
     p.in_range = ctx->in_range ? 1 : 0;
+    p.fp64 = (ctx->th.flags & HOUGH_FLAG_FP64) ? 1 : 0;
+    p.Cd = ctx->d_Cd;
+    p.Sd = ctx->d_Sd;
+    p.u_phi = (double)g.phi_u_per_deg;
+    p.u_z = (double)g.z_u_per_mm;
+    p.rho_min = g.rho_min;
+    p.drho = (g.rho_max - g.rho_min) / (double)ctx->n_rho;
     p.n_theta = ctx->n_theta;
     p.n_rho = ctx->n_rho;
     p.T = ctx->th.vote_threshold;
@@ -262,6 +269,13 @@ struct Prepared {
     unsigned grid;
 };
 
+// The find kernel of a context: fixed-point bins, or the FP64 variant.
+using FindKernel = void (*)(hk::KParams);
+static FindKernel find_kernel_of(const hough_ctx *ctx)
+{
+    return (ctx->th.flags & HOUGH_FLAG_FP64) ? hk::find_kernel<true> : hk::find_kernel<false>;
+}
+
 // Resolve a launch shape, raise the kernel's shared-memory limit and size the
 // persistent grid (not stream operations, so this runs outside any capture).
 int prepare_find(hough_ctx *ctx, int64_t n_windows, const hough_launch &req, Prepared &pr)
@@ -269,16 +283,16 @@ int prepare_find(hough_ctx *ctx, int64_t n_windows, const hough_launch &req, Pre
     int rc = resolve_launch(ctx, req, pr.l, pr.smem);
     if (rc != HOUGH_OK)
         return rc;
-    if (cudaFuncSetAttribute(hk::find_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)pr.smem) != cudaSuccess)
+    const FindKernel fk = find_kernel_of(ctx);
+    if (cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pr.smem) !=
+        cudaSuccess)
         return HOUGH_ERR_CUDA;
     cudaFuncAttributes fa{};
-    if (cudaFuncGetAttributes(&fa, hk::find_kernel) != cudaSuccess ||
-        fa.sharedSizeBytes > kStaticSmemReserve)
+    if (cudaFuncGetAttributes(&fa, fk) != cudaSuccess || fa.sharedSizeBytes > kStaticSmemReserve)
         return HOUGH_ERR_CUDA;
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hk::find_kernel, pr.l.threads,
-                                                      pr.smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fk, pr.l.threads, pr.smem) !=
+            cudaSuccess ||
         occ < 1)
         return HOUGH_ERR_UNSUPPORTED_SHAPE;
     long long grid = (long long)ctx->num_sms * std::min(occ, pr.l.ctas_per_sm);
@@ -291,7 +305,7 @@ int enqueue_find(hough_ctx *ctx, const hough_hits *hits, const int64_t *offsets,
                  unsigned int *counter, const Prepared &pr)
 {
     hk::KParams p = make_params(ctx, hits, offsets, n_windows, out, counter, pr.l);
-    hk::find_kernel<<<pr.grid, pr.l.threads, pr.smem, s>>>(p);
+    find_kernel_of(ctx)<<<pr.grid, pr.l.threads, pr.smem, s>>>(p);
     if (cudaGetLastError() != cudaSuccess)
         return HOUGH_ERR_CUDA;
     ctx->launches += 1;
@@ -434,6 +448,27 @@ int hough_create(const hough_geometry *g, int n_theta, int n_rho, const hough_th
         hough_destroy(ctx);
         return HOUGH_ERR_CUDA;
     }
+    if (th->flags & HOUGH_FLAG_FP64) {
+        // cos and sin of the row centres theta_t = (t + 1/2) pi / n_theta
+        std::vector<double> cd(n_theta), sd(n_theta);
+        for (int t = 0; t < n_theta; ++t) {
+            const double theta = ((double)t + 0.5) * (M_PI / (double)n_theta);
+            cd[t] = cos(theta);
+            sd[t] = sin(theta);
+        }
+        if (cudaMalloc(&ctx->d_Cd, sizeof(double) * n_theta) != cudaSuccess ||
+            cudaMalloc(&ctx->d_Sd, sizeof(double) * n_theta) != cudaSuccess) {
+            hough_destroy(ctx);
+            return HOUGH_ERR_ALLOC;
+        }
+        if (cudaMemcpy(ctx->d_Cd, cd.data(), sizeof(double) * n_theta, cudaMemcpyHostToDevice) !=
+                cudaSuccess ||
+            cudaMemcpy(ctx->d_Sd, sd.data(), sizeof(double) * n_theta, cudaMemcpyHostToDevice) !=
+                cudaSuccess) {
+            hough_destroy(ctx);
+            return HOUGH_ERR_CUDA;
+        }
+    }
     hough_launch l{};
     size_t smem = 0;
     rc = resolve_launch(ctx, hough_launch{}, l, smem);
@@ -457,6 +492,8 @@ void hough_destroy(hough_ctx *ctx)
         cudaFree(kv.second);
     cudaFree(ctx->d_C);
     cudaFree(ctx->d_S);
+    cudaFree(ctx->d_Cd);
+    cudaFree(ctx->d_Sd);
     cudaFree(ctx->stage_dev);
     cudaFree(ctx->d_cf);
     for (int i = 0; i < 2; ++i) {
@@ -529,7 +566,7 @@ int hough_find_noalloc(const hough_geometry *g, int n_theta, int n_rho,
                        const hough_tracks *tracks_out, void *stream)
 {
     if (!geometry_ok(g) || !th || th->vote_threshold < 1 || th->assoc_tol_bins < 0 ||
-        th->max_peaks < 0 || !hits_ok(hits) || n_windows < 0 ||
+        th->max_peaks < 0 || (th->flags & HOUGH_FLAG_FP64) || !hits_ok(hits) || n_windows < 0 ||
         n_windows >= (1ll << 31) - 65536 || (n_windows > 0 && !window_offsets))
         return HOUGH_ERR_INVALID_ARG;
     if (n_theta < 1 || n_theta > HOUGH_NOALLOC_MAX_THETA || n_rho < 4 || n_rho > HOUGH_MAX_RHO ||

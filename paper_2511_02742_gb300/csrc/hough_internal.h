@@ -20,6 +20,7 @@ struct hough_ctx {
     int K = 0;
     bool in_range = false;   // every valid hit votes inside [0, n_rho) in every row
     int32_t *d_C = nullptr, *d_S = nullptr;
+    double *d_Cd = nullptr, *d_Sd = nullptr;   // cos/sin of the row centres (HOUGH_FLAG_FP64)
     hough_launch launch{};
     int num_sms = 0;
     size_t smem_optin = 0;

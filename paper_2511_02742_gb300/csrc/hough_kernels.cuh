@@ -67,6 +67,12 @@ struct KParams {
     const int32_t *S;
     int D;              // tables at scale 2^K: every box hit's sum fits in int32
     int K;
+    // the FP64 variant (HOUGH_FLAG_FP64): cos/sin of the row centres and the
+    // units, for b = floor((phi/u_phi cos + z/u_z sin - rho_min) / drho)
+    const double *Cd;
+    const double *Sd;
+    double u_phi, u_z, rho_min, drho;
+    int fp64;
     int in_range;       // every valid hit votes inside [0, n_rho) in every row
     int n_theta, n_rho;
     int T, tol, max_peaks;
@@ -173,6 +179,20 @@ __device__ __forceinline__ bool load_hit(const KParams &p, long long i, int &phi
 // floor((phi*c + z*s + D) / 2^K): the tables' scale keeps the exact sum of
 // any hit of the detector box inside int32, so 32-bit wrap-around arithmetic
 // gives it exactly; the arithmetic shift is the floor division.
+__device__ __forceinline__ int rho_bin(int phi, int z, int c, int s, int D, int K);
+
+// The FP64 variant of the bin: Eq. (1) in double precision with the
+// Section 5 binning, each operation rounded to nearest in this order (no
+// fused multiply-add), so that it is reproducible: phi_deg = phi / u_phi and
+// z_mm = z / u_z once per hit, then per row
+// floor(((phi_deg cos + z_mm sin) - rho_min) / drho).
+__device__ __forceinline__ int rho_bin64(double phi_deg, double z_mm, double c, double s,
+                                         const KParams &p)
+{
+    const double rho = __dadd_rn(__dmul_rn(phi_deg, c), __dmul_rn(z_mm, s));
+    return __double2int_rd(__ddiv_rn(__dsub_rn(rho, p.rho_min), p.drho));
+}
+
 __device__ __forceinline__ int rho_bin(int phi, int z, int c, int s, int D, int K)
 {
     const unsigned v = (unsigned)phi * (unsigned)c + (unsigned)z * (unsigned)s + (unsigned)D;
@@ -252,7 +272,7 @@ __device__ __forceinline__ void list_append(uint32_t *seg, int L, int &cnt, cons
     }
 }
 
-template <int P, bool FAST>
+template <int P, bool FAST, bool F64 = false>
 __device__ void vote_tile(const KParams &p, uint32_t *acc, const int2 *stage, int nh, int t0,
                           uint32_t *seg, int L, int &cnt, const ListOvf &ovf, WinScalars &ws)
 {
@@ -264,13 +284,21 @@ __device__ void vote_tile(const KParams &p, uint32_t *acc, const int2 *stage, in
     const int wr = g * 32 + lane;
     const int hstep = nw / G;
     int c[P], s[P];
+    double cd[P], sd[P];
     bool act[P];
 #pragma unroll
     for (int k = 0; k < P; ++k) {
         int t = t0 + k * WR + wr;
         act[k] = t < p.n_theta;
-        c[k] = act[k] ? __ldg(p.C + t) : 0;
-        s[k] = act[k] ? __ldg(p.S + t) : 0;
+        if constexpr (F64) {
+            cd[k] = act[k] ? __ldg(p.Cd + t) : 0.0;
+            sd[k] = act[k] ? __ldg(p.Sd + t) : 0.0;
+            c[k] = s[k] = 0;
+        } else {
+            c[k] = act[k] ? __ldg(p.C + t) : 0;
+            s[k] = act[k] ? __ldg(p.S + t) : 0;
+            cd[k] = sd[k] = 0.0;
+        }
     }
     // bank-private column of this lane: word (wr, b) at col_word0 + 32 b
     const unsigned col_word0 = (unsigned)(g * p.n_rho) * 32u + (unsigned)lane;
@@ -291,9 +319,17 @@ __device__ void vote_tile(const KParams &p, uint32_t *acc, const int2 *stage, in
         int bb[P];
         bool in[P];
         unsigned old[P];
+        double phd = 0.0, zmm = 0.0;
+        if constexpr (F64) {
+            phd = __ddiv_rn((double)hv.x, p.u_phi);
+            zmm = __ddiv_rn((double)hv.y, p.u_z);
+        }
 #pragma unroll
         for (int k = 0; k < P; ++k) {
-            bb[k] = rho_bin(hv.x, hv.y, c[k], s[k], D, K);
+            if constexpr (F64)
+                bb[k] = rho_bin64(phd, zmm, cd[k], sd[k], p);
+            else
+                bb[k] = rho_bin(hv.x, hv.y, c[k], s[k], D, K);
             in[k] = true;
             if (!FAST) {
                 in[k] = act[k] && (unsigned)bb[k] < nr;
@@ -820,7 +856,7 @@ __device__ void check_direct(const KParams &p, const TileView<P> &tv, int rlo, i
 
 // Returns the number of valid hits left in `stage` (in their original order),
 // or -1 when the window was streamed through the stage in parts.
-template <int P>
+template <int P, bool F64>
 __device__ int process_tiles(const KParams &p, long long beg, int H, uint32_t *acc, int2 *stage,
                               int *carry, unsigned long long *keys, uint32_t *cl,
                               unsigned long long *top_stage, WarpCounters wc, int *vh,
@@ -854,21 +890,21 @@ __device__ int process_tiles(const KParams &p, long long beg, int H, uint32_t *a
         int cnt = 0;        // this lane's column entries (a register)
         const int L = (p.seg_cl - p.seg_ovf) >> 5;
         const ListOvf ovf{wc.n_ovf + warp, p.seg_ovf};
-        const bool fast = p.in_range && t0 + R <= p.n_theta;
+        const bool fast = !F64 && p.in_range && t0 + R <= p.n_theta;
         TileView<P> tv{acc, carry0, carry1, t0, R, p.lw, p.n_theta, p.n_rho};
         const int rlo = max(t0 - 1, 0);
         const int rhi = last ? p.n_theta : t0 + R - 1;
         const int ihi = rhi - t0;
         if (single) {
             if (fast)
-                vote_tile<P, true>(p, acc, stage, nv, t0, my_cl, L, cnt, ovf, ws);
+                vote_tile<P, !F64, F64>(p, acc, stage, nv, t0, my_cl, L, cnt, ovf, ws);
             else
-                vote_tile<P, false>(p, acc, stage, nv, t0, my_cl, L, cnt, ovf, ws);
+                vote_tile<P, false, F64>(p, acc, stage, nv, t0, my_cl, L, cnt, ovf, ws);
         } else {
             for (long long s0 = 0; s0 < H; s0 += p.hit_stage) {
                 int n = (int)min((long long)p.hit_stage, (long long)H - s0);
                 int ns = stage_hits(p, beg + s0, n, stage, wtot, ws);
-                vote_tile<P, false>(p, acc, stage, ns, t0, my_cl, L, cnt, ovf, ws);
+                vote_tile<P, false, F64>(p, acc, stage, ns, t0, my_cl, L, cnt, ovf, ws);
                 __syncthreads();
             }
         }
@@ -1002,6 +1038,7 @@ __device__ int process_tiles(const KParams &p, long long beg, int H, uint32_t *a
 // the hits: it counts its categories (wcat, one row per warp), a prefix over
 // categories and then over warps gives every (warp, category) its first
 // slot, and the warp scatters its slice in order.
+template <bool F64>
 __device__ void associate(const KParams &p, long long w, long long beg, int H, int n_top,
                           const unsigned long long *keys, int *pk, const int2 *hits_s,
                           int *cat_s, int *wcat, int *cat_base)
@@ -1044,8 +1081,18 @@ __device__ void associate(const KParams &p, long long w, long long beg, int H, i
         }
         int first = n_top;
         if (ok) {
+            double phd = 0.0, zmm = 0.0;
+            if constexpr (F64) {
+                phd = __ddiv_rn((double)phi, p.u_phi);
+                zmm = __ddiv_rn((double)z, p.u_z);
+            }
             for (int q = sub; q < n_top; q += 4) {
-                int d = rho_bin(phi, z, pk_c[q], pk_s[q], D, K) - pk_b[q];
+                int d;
+                if constexpr (F64)
+                    d = rho_bin64(phd, zmm, __ldg(p.Cd + pk_t[q]), __ldg(p.Sd + pk_t[q]), p) -
+                        pk_b[q];
+                else
+                    d = rho_bin(phi, z, pk_c[q], pk_s[q], D, K) - pk_b[q];
                 if (d <= tol && d >= -tol) {
                     first = q;
                     break;
@@ -1141,6 +1188,9 @@ __device__ void associate(const KParams &p, long long w, long long beg, int H, i
     __syncthreads();
 }
 
+// F64: the FP64 variant of the bins (HOUGH_FLAG_FP64), a kernel of its own so
+// that its registers do not weigh on the fixed-point kernel.
+template <bool F64>
 __global__ void __launch_bounds__(1024, 1) find_kernel(KParams p)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1190,12 +1240,21 @@ __global__ void __launch_bounds__(1024, 1) find_kernel(KParams p)
                 vh[i] = 0;
             __syncthreads();
             int nv;
-            if (H <= 255)
-                nv = process_tiles<4>(p, beg, H, acc, stage, carry, keys, cl, top_stage, wc, vh, wtot, ws, w);
-            else if (H <= 65535)
-                nv = process_tiles<2>(p, beg, H, acc, stage, carry, keys, cl, top_stage, wc, vh, wtot, ws, w);
-            else
-                nv = process_tiles<1>(p, beg, H, acc, stage, carry, keys, cl, top_stage, wc, vh, wtot, ws, w);
+            if constexpr (F64) {
+                if (H <= 255)
+                    nv = process_tiles<4, true>(p, beg, H, acc, stage, carry, keys, cl, top_stage, wc, vh, wtot, ws, w);
+                else if (H <= 65535)
+                    nv = process_tiles<2, true>(p, beg, H, acc, stage, carry, keys, cl, top_stage, wc, vh, wtot, ws, w);
+                else
+                    nv = process_tiles<1, true>(p, beg, H, acc, stage, carry, keys, cl, top_stage, wc, vh, wtot, ws, w);
+            } else {
+                if (H <= 255)
+                    nv = process_tiles<4, false>(p, beg, H, acc, stage, carry, keys, cl, top_stage, wc, vh, wtot, ws, w);
+                else if (H <= 65535)
+                    nv = process_tiles<2, false>(p, beg, H, acc, stage, carry, keys, cl, top_stage, wc, vh, wtot, ws, w);
+                else
+                    nv = process_tiles<1, false>(p, beg, H, acc, stage, carry, keys, cl, top_stage, wc, vh, wtot, ws, w);
+            }
             __syncthreads();
             const int n_top = ws.n_top;
             // the tile and the list area are free now: the per-warp category
@@ -1211,7 +1270,10 @@ __global__ void __launch_bounds__(1024, 1) find_kernel(KParams p)
                 wcat = reinterpret_cast<int *>(cl);
                 cat_s = H + need <= p.cl_total ? reinterpret_cast<int *>(cl) + need : nullptr;
             }
-            associate(p, w, beg, H, n_top, keys, pk, nv == H ? stage : nullptr, cat_s, wcat, cnt);
+            if constexpr (F64)
+                associate<true>(p, w, beg, H, n_top, keys, pk, nv == H ? stage : nullptr, cat_s, wcat, cnt);
+            else
+                associate<false>(p, w, beg, H, n_top, keys, pk, nv == H ? stage : nullptr, cat_s, wcat, cnt);
             if (threadIdx.x == 0) {
                 int found = 0;
                 for (int k = 0; k < nw; ++k)

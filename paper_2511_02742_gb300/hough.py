@@ -32,6 +32,7 @@ HOUGH_EXT_MAX_HITS = 4096
 HOUGH_EXT_MAX_VANES = 256
 HOUGH_EXT_MAX_TOL = (1 << 19) - 1
 HOUGH_FLAG_EXPORT_ACC = 1
+HOUGH_FLAG_FP64 = 2
 HOUGH_ERR_TIMEOUT = -4
 HOUGH_ERR_UNSUPPORTED_SHAPE = -5
 HOUGH_ERR_BUSY = -7
@@ -387,13 +388,13 @@ class Finder:
     """One context (accumulator shape + thresholds) on the current CUDA device."""
 
     def __init__(self, n_theta: int, n_rho: int, geometry: dict | None = None, vote_threshold=5,
-                 assoc_tol_bins=1, max_peaks=64, export_acc=False):
+                 assoc_tol_bins=1, max_peaks=64, export_acc=False, fp64=False):
         from .synth import GEOMETRY
         self.geometry = dict(GEOMETRY if geometry is None else geometry)
         self.n_theta, self.n_rho = n_theta, n_rho
         self.max_peaks = max_peaks
         self.export_acc = export_acc
-        flags = HOUGH_FLAG_EXPORT_ACC if export_acc else 0
+        flags = (HOUGH_FLAG_EXPORT_ACC if export_acc else 0) | (HOUGH_FLAG_FP64 if fp64 else 0)
         self.ctx = hough_create(self.geometry, n_theta, n_rho, vote_threshold, assoc_tol_bins,
                                 max_peaks, flags)
 
