@@ -14,21 +14,29 @@ from paper_2511_02742_gb300 import synth
 G = synth.GEOMETRY
 
 
-def numpy_bins(n_theta, n_rho, phi_q, z_q):
+def numpy_bins(n_theta, n_rho, phi_q, z_q, geom=G):
     theta = (np.arange(n_theta) + 0.5) * (math.pi / n_theta)
-    phi = np.asarray(phi_q, np.float64) / G["phi_u_per_deg"]
-    z = np.asarray(z_q, np.float64) / G["z_u_per_mm"]
+    phi = np.asarray(phi_q, np.float64) / geom["phi_u_per_deg"]
+    z = np.asarray(z_q, np.float64) / geom["z_u_per_mm"]
     rho = phi[:, None] * np.cos(theta)[None, :] + z[:, None] * np.sin(theta)[None, :]
-    x = (rho - G["rho_min"]) / ((G["rho_max"] - G["rho_min"]) / n_rho)
+    x = (rho - geom["rho_min"]) / ((geom["rho_max"] - geom["rho_min"]) / n_rho)
     return x
 
 
-@pytest.mark.parametrize("n_theta,n_rho", [(180, 1000), (256, 256), (97, 332)])
-def test_fp64_accumulator_is_the_histogram_of_eq1(n_theta, n_rho):
+@pytest.mark.parametrize("n_theta,n_rho,rho_half", [(180, 1000, 500.0), (256, 256, 500.0),
+                                                    (97, 332, 500.0), (128, 256, 250.0)])
+def test_fp64_accumulator_is_the_histogram_of_eq1(n_theta, n_rho, rho_half):
+    """Random hits of the box plus hits outside it (which do not vote); with a
+    narrower rho range some votes fall below rho_min and are dropped."""
+    geom = dict(G, rho_min=-rho_half, rho_max=rho_half)
     rng = np.random.default_rng(21)
     phi = rng.integers(0, 360 * 200, 300).astype(np.int32)
     z = rng.integers(-38912, 38912 + 1, 300).astype(np.int32)
-    x = numpy_bins(n_theta, n_rho, phi, z)
+    phi[:10] = 72000 + rng.integers(0, 500, 10)                # outside the box
+    z[10:20] = 39000 + rng.integers(0, 500, 10)
+    valid = np.ones(300, bool)
+    valid[:20] = False
+    x = numpy_bins(n_theta, n_rho, phi, z, geom)[valid]
     frac = x - np.floor(x)
     assert ((frac > 1e-9) & (frac < 1 - 1e-9)).all()     # no value on an edge
     b = np.floor(x).astype(np.int64)
@@ -36,9 +44,33 @@ def test_fp64_accumulator_is_the_histogram_of_eq1(n_theta, n_rho):
     t = np.broadcast_to(np.arange(n_theta)[None, :], b.shape)
     ok = (b >= 0) & (b < n_rho)
     np.add.at(ref, (t[ok], b[ok]), 1)
-    r = oracle.find_window(G, n_theta, n_rho, phi, z, fp64=True)
+    r = oracle.find_window(geom, n_theta, n_rho, phi, z, fp64=True)
     np.testing.assert_array_equal(r["acc"], ref)
     assert r["n_dropped"] == int((~ok).sum())
+    if rho_half < 409:
+        assert (x < 0).any()                # votes below rho_min: floor, not truncation
+
+
+def test_fp64_association_uses_the_fp64_bins():
+    """Each hit goes to the first peak (in order) whose row's FP64 bin, from
+    the independent numpy evaluation, is within one bin of the peak's."""
+    w = synth.generate(60, ("poisson", 10, 1, 40), (100.0, 300.0), 0.02, seed=26)
+    phi, z = oracle.encode(G, w.vane, w.strip)
+    r = oracle.find_batch(G, 256, 256, phi, z, w.offsets, fp64=True)
+    checked = 0
+    for k in range(w.n_windows):
+        s = w.window(k)
+        x = numpy_bins(256, 256, phi[s], z[s])
+        frac = x - np.floor(x)
+        if not ((frac > 1e-9) & (frac < 1 - 1e-9)).all():
+            continue
+        b = np.floor(x).astype(np.int64)
+        pk = r["peaks"][k][:r["n_peaks"][k]]
+        for h in range(s.stop - s.start):
+            m = np.flatnonzero(np.abs(b[h, pk["theta"].astype(int)] - pk["rho"].astype(int)) <= 1)
+            assert r["hit_track"][s][h] == (m[0] if len(m) else -1)
+            checked += 1
+    assert checked > 3000
 
 
 def test_fp64_and_fixed_accumulators_differ_by_votes_moved_one_bin():
