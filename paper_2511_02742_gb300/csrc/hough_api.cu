@@ -851,8 +851,14 @@ int hough_time_slice(hough_ctx *ctx, const int64_t *t, const int32_t *in0, const
     q.out_index = reinterpret_cast<long long *>(out_index);
     q.offsets = reinterpret_cast<long long *>(window_offsets);
     q.status = status;
-    const long long warps_needed = n_windows + 1;
-    const long long blocks = std::min<long long>((warps_needed + 7) / 8, (long long)ctx->num_sms * 8);
+    // blocks of consecutive windows per CTA step: the largest power of two
+    // (32 to kSliceBlock) that still gives every SM eight of them
+    int B = hk::kSliceBlock;
+    while (B > 32 && (n_windows + 1) / B < 8LL * ctx->num_sms)
+        B >>= 1;
+    q.block = B;
+    const long long blocks = std::min<long long>((n_windows + 1 + B - 1) / B,
+                                                 (long long)ctx->num_sms * 8);
     hk::slice_kernel<<<(unsigned)std::max<long long>(blocks, 1), 256, 0, s>>>(q);
     if (cudaGetLastError() != cudaSuccess)
         return fail(ctx, HOUGH_ERR_CUDA);

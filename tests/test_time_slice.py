@@ -91,3 +91,36 @@ def test_edges_empty_stream_and_unsorted(hough):
         f.time_slice(_dev(t), dict(vane=_dev(vane), strip=_dev(strip)), 0, 10, 25, 4)
     assert ex.value.code == hough.HOUGH_ERR_UNSUPPORTED_SHAPE
     f.close()
+
+
+@pytest.mark.parametrize("rate,m,W", [(0.002, 2, 257), (0.6, 16, 1500), (0.05, 3, 256),
+                                      (0.6, 1, 1), (0.3, 7, 2049)])
+def test_blocks_gaps_and_duplicate_times(hough, rate, m, W):
+    """Window counts around the slicer's block of 256 windows, sparse streams
+    (many window starts between two hits), the longest overlap, and repeated
+    times (a lower bound takes the first of equal times)."""
+    step = 5000
+    s = synth.timed_stream(W * step / 1000.0 + 50, rate, noise_frac=0.02, seed=W)
+    t = s.t.copy()
+    t[1::7] = t[0::7][:len(t[1::7])]            # repeat some times (still sorted)
+    t = np.maximum.accumulate(t)
+    f = hough.Finder(256, 256)
+    r = _slice(f, synth.TimedHits(t, s.vane, s.strip, s.track), -777, step, m * step, W)
+    offs, idx = oracle.time_slice(t, -777, step, m * step, W)
+    np.testing.assert_array_equal(r["offsets"].cpu().numpy(), offs)
+    np.testing.assert_array_equal(r["index"].cpu().numpy()[:len(idx)], idx)
+    assert int(r["status"].item()) == 0
+    f.close()
+
+
+def test_extreme_times(hough):
+    """Times near the ends of int64 lie before or after every window."""
+    big = np.iinfo(np.int64)
+    t = np.array([big.min, big.min + 5, -20, 0, 3, 3, 17, 29, big.max - 9, big.max], np.int64)
+    vane = np.arange(len(t), dtype=np.int32)
+    f = hough.Finder(256, 256)
+    r = _slice(f, synth.TimedHits(t, vane, vane, np.zeros(len(t), np.int64)), 0, 10, 20, 5)
+    offs, idx = oracle.time_slice(t, 0, 10, 20, 5)
+    np.testing.assert_array_equal(r["offsets"].cpu().numpy(), offs)
+    np.testing.assert_array_equal(r["index"].cpu().numpy()[:len(idx)], idx)
+    f.close()
