@@ -22,6 +22,7 @@
 #include "hough_coarse_fine.cuh"
 #include "hough_iterative.cuh"
 #include "hough_extend.cuh"
+#include "hough_slice.cuh"
 
 // Whether every valid hit votes inside [0, n_rho) in every row: the bin is
 // monotone in phi and in z, so the four corners of the detector box bound it.
