@@ -872,7 +872,7 @@ def main():
     ap.add_argument("--serve-pool", type=int, default=20000)
     ap.add_argument("--serve-launch", default="",
                     help="threads,word_rows,hit_stage,ctas_per_sm for the serving context")
-    ap.add_argument("--slice-us", type=float, default=100.0)
+    ap.add_argument("--slice-us", type=float, default=1000.0)
     ap.add_argument("--no-coarse-fine", dest="coarse_fine", action="store_false")
     ap.add_argument("--iter-windows", type=int, default=20000)
     ap.add_argument("--no-extend", dest="extend", action="store_false",
