@@ -233,6 +233,51 @@ def hough_destroy(ctx) -> None:
     load().hough_destroy(ctx)
 
 
+def _check_buf(x, dtype, min_numel: int, cuda: bool, name: str) -> None:
+    """A buffer handed to the library must be a contiguous torch tensor of the
+    given dtype, on the GPU (device entry points) or in host memory (host
+    entry points), with at least min_numel elements: the kernels trust the
+    pointers and sizes they get."""
+    import torch
+    if not isinstance(x, torch.Tensor):
+        raise TypeError(f"{name}: a torch tensor is needed, got {type(x).__name__}")
+    if x.dtype != dtype:
+        raise TypeError(f"{name}: dtype {x.dtype}, expected {dtype}")
+    if not x.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if x.is_cuda != cuda:
+        raise ValueError(f"{name}: must be {'on the GPU' if cuda else 'in host memory'}")
+    if x.numel() < min_numel:
+        raise ValueError(f"{name}: {x.numel()} elements, at least {min_numel} needed")
+
+
+def _check_hits(hits: dict, cuda: bool) -> int:
+    import torch
+    keys = ("vane", "strip") if "vane" in hits else ("phi_q", "z_q")
+    n = int(hits[keys[0]].numel()) if hasattr(hits[keys[0]], "numel") else -1
+    for k in keys:
+        _check_buf(hits[k], torch.int32, n, cuda, k)
+    if int(hits[keys[1]].numel()) != n:
+        raise ValueError(f"{keys[0]} and {keys[1]} differ in length")
+    return n
+
+
+def _check_outputs(out: dict, n_windows: int, n_hits: int, max_peaks: int, export: tuple | None,
+                   cuda: bool) -> None:
+    import torch
+    i32 = torch.int32
+    if max_peaks > 0:
+        _check_buf(out.get("peaks"), i32, n_windows * max_peaks * 4, cuda, "peaks")
+    _check_buf(out.get("n_peaks"), i32, n_windows, cuda, "n_peaks")
+    if out.get("n_found") is not None:
+        _check_buf(out["n_found"], i32, n_windows, cuda, "n_found")
+    _check_buf(out.get("window_status"), i32, n_windows, cuda, "window_status")
+    _check_buf(out.get("hit_track"), i32, n_hits, cuda, "hit_track")
+    _check_buf(out.get("track_hits"), i32, n_hits, cuda, "track_hits")
+    if export is not None:
+        _check_buf(out.get("acc"), i32, n_windows * export[0] * export[1], cuda, "acc")
+
+
 def make_hits(phi_q=None, z_q=None, vane=None, strip=None, n_hits=None) -> hough_hits:
     if n_hits is None:
         n_hits = len(vane) if vane is not None else len(phi_q)
@@ -434,21 +479,28 @@ class Finder:
         return make_hits(phi_q=hits["phi_q"], z_q=hits["z_q"], n_hits=hits["phi_q"].numel()
                          if hasattr(hits["phi_q"], "numel") else len(hits["phi_q"]))
 
-    def find(self, hits: dict, offsets, out: dict | None = None, stream=None) -> dict:
-        n_windows = int(offsets.numel() if hasattr(offsets, "numel") else len(offsets)) - 1
-        hs = self.hits_struct(hits)
+    def _checked(self, hits: dict, offsets, out: dict | None, cuda: bool) -> tuple:
+        """Check the buffers of a find call; returns (n_windows, n_hits, out)."""
+        import torch
+        n_hits = _check_hits(hits, cuda)
+        _check_buf(offsets, torch.int64, 1, cuda, "offsets")
+        n_windows = int(offsets.numel()) - 1
         if out is None:
-            out = self.alloc_outputs(n_windows, hs.n_hits)
-        hough_find(self.ctx, hs, offsets, n_windows, make_tracks(out), stream)
+            out = self.alloc_outputs(n_windows, n_hits, device="cuda" if cuda else "cpu", pin=not cuda)
+        _check_outputs(out, n_windows, n_hits, self.max_peaks,
+                       (self.n_theta, self.n_rho) if self.export_acc else None, cuda)
+        return n_windows, n_hits, out
+
+    def find(self, hits: dict, offsets, out: dict | None = None, stream=None) -> dict:
+        n_windows, _, out = self._checked(hits, offsets, out, cuda=True)
+        hough_find(self.ctx, self.hits_struct(hits), offsets, n_windows, make_tracks(out), stream)
         return out
 
     def find_host(self, hits: dict, offsets, out: dict | None = None, stream=None) -> dict:
         """End-to-end form: host (ideally pinned) buffers in and out."""
-        n_windows = int(offsets.numel() if hasattr(offsets, "numel") else len(offsets)) - 1
-        hs = self.hits_struct(hits)
-        if out is None:
-            out = self.alloc_outputs(n_windows, hs.n_hits, device="cpu")
-        hough_find_host(self.ctx, hs, offsets, n_windows, make_tracks(out), stream)
+        n_windows, _, out = self._checked(hits, offsets, out, cuda=False)
+        hough_find_host(self.ctx, self.hits_struct(hits), offsets, n_windows, make_tracks(out),
+                        stream)
         return out
 
     def extend(self, hits: dict, offsets, found: dict, tol_z: int, out: dict | None = None,
@@ -456,7 +508,10 @@ class Finder:
         """Track extension (hough_extend) on the outputs of find() for the same
         hits and windows; returns dict(tracks, ext_track, ext_hits, window_status)."""
         import torch
+        n_hits = _check_hits(hits, True)
+        _check_buf(offsets, torch.int64, 1, True, "offsets")
         n_windows = int(offsets.numel()) - 1
+        _check_outputs(found, n_windows, n_hits, self.max_peaks, None, True)
         hs = self.hits_struct(hits)
         if out is None:
             dev = found["n_peaks"].device
@@ -466,11 +521,15 @@ class Finder:
                 ext_track=torch.zeros(max(hs.n_hits, 1), dtype=torch.int32, device=dev),
                 ext_hits=torch.zeros(max(hs.n_hits, 1), dtype=torch.int32, device=dev),
                 window_status=torch.zeros(max(n_windows, 1), dtype=torch.int32, device=dev))
+        _check_buf(out.get("tracks"), torch.int32, n_windows * self.max_peaks * 4, True, "tracks")
+        _check_buf(out.get("ext_track"), torch.int32, n_hits, True, "ext_track")
+        _check_buf(out.get("ext_hits"), torch.int32, n_hits, True, "ext_hits")
+        _check_buf(out.get("window_status"), torch.int32, n_windows, True, "window_status")
         hough_extend(self.ctx, hs, offsets, n_windows, make_tracks(found), tol_z, out, stream)
         return out
 
     def plan(self, hits: dict, offsets, out: dict, stream=None):
-        n_windows = int(offsets.numel()) - 1
+        n_windows, _, out = self._checked(hits, offsets, out, cuda=True)
         return hough_plan_create(self.ctx, self.hits_struct(hits), offsets, n_windows,
                                  make_tracks(out), stream)
 
@@ -480,7 +539,10 @@ class Finder:
         windows; returns dict(hits=..., offsets, index, status, capacity) ready
         for find()."""
         import torch
+        _check_buf(t, torch.int64, 0, True, "t")
         n = int(t.numel())
+        if _check_hits(hits, True) != n:
+            raise ValueError("the hits and their times differ in length")
         cap = max(1, n * (length // step))
         raw = "vane" in hits
         a, b = (hits["vane"], hits["strip"]) if raw else (hits["phi_q"], hits["z_q"])
@@ -496,7 +558,7 @@ class Finder:
         return dict(hits=sliced, offsets=offs, index=idx, status=status, capacity=cap)
 
     def autotune(self, hits: dict, offsets, out: dict, iters=3, stream=None) -> dict:
-        n_windows = int(offsets.numel()) - 1
+        n_windows, _, out = self._checked(hits, offsets, out, cuda=True)
         return hough_autotune(self.ctx, self.hits_struct(hits), offsets, n_windows,
                               make_tracks(out), iters, stream)
 

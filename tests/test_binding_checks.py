@@ -1,0 +1,40 @@
+"""The Python binding refuses buffers the kernels could misread: wrong dtype,
+not contiguous, on the wrong side of the bus, or too small (no GPU needed:
+the checks run before any call into the library)."""
+import pytest
+import torch
+
+from paper_2511_02742_gb300 import hough
+
+
+def test_buffer_checks():
+    ok = torch.zeros(10, dtype=torch.int32)
+    hough._check_buf(ok, torch.int32, 10, False, "x")
+    with pytest.raises(TypeError):
+        hough._check_buf(ok.numpy(), torch.int32, 1, False, "x")
+    with pytest.raises(TypeError):
+        hough._check_buf(ok.to(torch.int64), torch.int32, 1, False, "x")
+    with pytest.raises(ValueError):
+        hough._check_buf(torch.zeros((4, 4), dtype=torch.int32).t(), torch.int32, 1, False, "x")
+    with pytest.raises(ValueError):
+        hough._check_buf(ok, torch.int32, 11, False, "x")
+    with pytest.raises(ValueError):
+        hough._check_buf(ok, torch.int32, 1, True, "x")       # host tensor for a device call
+
+
+def test_hits_and_outputs_checks():
+    v = torch.zeros(5, dtype=torch.int32)
+    assert hough._check_hits(dict(vane=v, strip=v), False) == 5
+    with pytest.raises(ValueError):
+        hough._check_hits(dict(vane=v, strip=torch.zeros(4, dtype=torch.int32)), False)
+    i32 = torch.int32
+    out = dict(peaks=torch.zeros((3, 8, 4), dtype=i32), n_peaks=torch.zeros(3, dtype=i32),
+               n_found=None, window_status=torch.zeros(3, dtype=i32),
+               hit_track=torch.zeros(5, dtype=i32), track_hits=torch.zeros(5, dtype=i32))
+    hough._check_outputs(out, 3, 5, 8, None, False)
+    with pytest.raises(ValueError):
+        hough._check_outputs(out, 3, 5, 9, None, False)       # peaks too small for 9 per window
+    with pytest.raises(ValueError):
+        hough._check_outputs(out, 3, 6, 8, None, False)       # per-hit outputs too small
+    with pytest.raises(TypeError):
+        hough._check_outputs(out, 3, 5, 8, (4, 4), False)     # no accumulator given
