@@ -251,6 +251,23 @@ def _check_buf(x, dtype, min_numel: int, cuda: bool, name: str) -> None:
         raise ValueError(f"{name}: {x.numel()} elements, at least {min_numel} needed")
 
 
+def _check_host(x, dtype, min_numel: int, name: str) -> None:
+    """A host buffer: a contiguous numpy array, or a torch tensor in host
+    memory, of the given dtype and at least min_numel elements."""
+    if isinstance(x, np.ndarray):
+        ok = x.dtype == dtype and x.flags.c_contiguous
+        size = x.size
+    elif hasattr(x, "is_cuda") and hasattr(x, "numpy"):
+        ok = (not x.is_cuda) and x.is_contiguous() and x.numpy().dtype == dtype
+        size = int(x.numel())
+    else:
+        ok, size = False, 0
+    if not ok:
+        raise TypeError(f"{name}: a contiguous host array of {np.dtype(dtype)} is needed")
+    if size < min_numel:
+        raise ValueError(f"{name}: {size} elements, at least {min_numel} needed")
+
+
 def _check_hits(hits: dict, cuda: bool) -> int:
     import torch
     keys = ("vane", "strip") if "vane" in hits else ("phi_q", "z_q")
@@ -597,7 +614,21 @@ class Server:
         starting at 0); results go to the host arrays of `out` (as Finder
         outputs).  Raises HoughError (code HOUGH_ERR_BUSY when the queue is full)."""
         offsets = np.ascontiguousarray(offsets, np.int64)
-        req = hough_request(_ptr(in0), _ptr(in1), _ptr(offsets), len(offsets) - 1,
+        n_windows = len(offsets) - 1
+        n_hits = int(offsets[-1]) if n_windows >= 0 else 0
+        # the worker reads the inputs and writes the outputs through these
+        # pointers: check types and sizes here (the library checks the offsets)
+        for name, x, dt, n in [("in0", in0, np.int32, n_hits), ("in1", in1, np.int32, n_hits),
+                               ("n_peaks", out.get("n_peaks"), np.int32, n_windows),
+                               ("window_status", out.get("window_status"), np.int32, n_windows),
+                               ("hit_track", out.get("hit_track"), np.int32, n_hits),
+                               ("track_hits", out.get("track_hits"), np.int32, n_hits),
+                               ("peaks", out.get("peaks"), np.int32,
+                                n_windows * self.finder.max_peaks * 4)]:
+            _check_host(x, dt, n, name)
+        if out.get("n_found") is not None:
+            _check_host(out["n_found"], np.int32, n_windows, "n_found")
+        req = hough_request(_ptr(in0), _ptr(in1), _ptr(offsets), n_windows,
                             make_tracks(out), int(arrival_ns))
         t = ctypes.c_uint64()
         _check(self.lib.hough_server_submit(self.h, ctypes.byref(req), ctypes.byref(t)),

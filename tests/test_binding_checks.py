@@ -38,3 +38,15 @@ def test_hits_and_outputs_checks():
         hough._check_outputs(out, 3, 6, 8, None, False)       # per-hit outputs too small
     with pytest.raises(TypeError):
         hough._check_outputs(out, 3, 5, 8, (4, 4), False)     # no accumulator given
+
+
+def test_host_buffer_checks():
+    import numpy as np
+    hough._check_host(np.zeros(3, np.int32), np.int32, 3, "a")
+    hough._check_host(torch.zeros(3, dtype=torch.int32), np.int32, 3, "b")
+    for bad in (np.zeros(3, np.int64), torch.zeros(3, dtype=torch.int64), [1, 2, 3],
+                np.zeros((3, 2), np.int32)[:, 0]):
+        with pytest.raises(TypeError):
+            hough._check_host(bad, np.int32, 1, "c")
+    with pytest.raises(ValueError):
+        hough._check_host(np.zeros(2, np.int32), np.int32, 3, "d")

@@ -176,3 +176,25 @@ def test_admission_limits_and_errors():
         hough.Server(fe, n_slots=1, slot_windows=8, slot_hits=1024)
     fe.close()
     f.close()
+
+
+def test_request_buffers_are_checked_before_submission():
+    """The worker reads and writes a request through its pointers, so wrong
+    types and short arrays are refused at submission."""
+    from paper_2511_02742_gb300 import hough
+    w = synth.workload("batched", n_windows=20, seed=5)
+    f = hough.Finder(512, 512)
+    srv = hough.Server(f, n_slots=1, slot_windows=64, slot_hits=1 << 16, max_queued=4)
+    try:
+        out = _host_out(f, 20, w.n_hits)
+        with pytest.raises(TypeError):
+            srv.submit(w.vane.astype(np.int64), w.strip, w.offsets, out)
+        short = dict(out, hit_track=out["hit_track"][: w.n_hits - 1])
+        with pytest.raises(ValueError):
+            srv.submit(w.vane, w.strip, w.offsets, short)
+        with pytest.raises(ValueError):
+            srv.submit(w.vane[:-1], w.strip[:-1], w.offsets, out)
+        t = srv.submit(w.vane, w.strip, w.offsets, out)
+        assert srv.wait(t, 60000)["status"] == 0
+    finally:
+        srv.close()
