@@ -152,7 +152,7 @@ def _cpu_baseline(w, n_theta, n_rho, budget_s=12.0):
             "sample_single_core": f"first {n1} windows, 1 thread ({dt1:.1f} s)"}
 
 
-def _iterative_leg(args, dev, stream, w, hits, offs, out_find):
+def _iterative_leg(args, dev, stream, w, hits, offs, out_find, smem_peak):
     """The iterative highest-bin search on the first --iter-windows windows of
     the batch, and how many of its tracks are peaks of the local-maximum
     search (same bin)."""
@@ -186,10 +186,29 @@ def _iterative_leg(args, dev, stream, w, hits, offs, out_find):
             total += 1
             match += (int(trv[k][j]["theta"]), int(trv[k][j]["rho"])) in peaks
     f.close()
+    # every iteration votes the hits still unassigned, in every theta row;
+    # the last one (no line left) too unless max_tracks was reached
+    valid = (w.vane >= 0) & (w.vane < synth.N_VANES) & (w.strip >= 0) & \
+        (w.strip < synth.N_Z_STRIPS)
+    votes = 0
+    for k in range(n):
+        h = int(valid[w.offsets[k]:w.offsets[k + 1]].sum())
+        taken = trv[k]["n_hits"][:ntv[k]]
+        for j in range(ntv[k] + (1 if ntv[k] < mt else 0)):
+            votes += h
+            if j < ntv[k]:
+                h -= int(taken[j])
+    votes *= cfg["n_theta"]
+    rate = votes / (ms * 1e-3) / 1e9
     return {"method": "iterative highest bin: vote, argmax, take its line's hits, re-vote",
             "windows": n, "ms": round(ms, 3), "windows_per_s": round(n / (ms * 1e-3), 1),
             "mean_tracks_per_window": round(float(ntv.mean()), 2),
-            "tracks_that_are_local_max_peaks": round(match / max(total, 1), 4)}
+            "tracks_that_are_local_max_peaks": round(match / max(total, 1), 4),
+            "roofline": {"bound": "alu", "achieved": round(rate, 2), "peak": smem_peak["value"],
+                         "unit": "Gvote/s",
+                         "frac": round(rate / smem_peak["value"], 4) if smem_peak["value"] else None,
+                         "algorithmic": f"{votes} shared-memory votes (each iteration votes the "
+                                        "unassigned hits in every row)"}}
 
 
 def _extension_leg(args, dev, stream, flush, w, hits, offs, out_find, hbm_gbs):
@@ -312,7 +331,7 @@ def _fp64_leg(args, dev, stream, w, hits, offs, out_find):
             "top_peak_same_bin": round(same / max(cmp, 1), 4)}
 
 
-def _coarse_fine_leg(args, dev, stream, flush, w, hits, offs):
+def _coarse_fine_leg(args, dev, stream, flush, w, hits, offs, smem_peak):
     """The paper's own two-stage search (coarse 18 x 100, then 10 x 10 of the
     180 x 1000 grid; one line per window) on the same batch, and how often its
     line is the top peak of the full 180 x 1000 search of this library."""
@@ -348,11 +367,26 @@ def _coarse_fine_leg(args, dev, stream, flush, w, hits, offs):
     same = both & (tt == lv["fine_theta"]) & (rr == lv["fine_rho"])
     near = both & (np.abs(tt - lv["fine_theta"]) <= 1) & (np.abs(rr - lv["fine_rho"]) <= 1)
     f.close()
+    # votes: every valid hit in the 18 coarse rows, and in the 10 fine rows of
+    # the windows whose coarse maximum reached T
+    from paper_2511_02742_gb300 import synth
+    valid = (w.vane >= 0) & (w.vane < synth.N_VANES) & (w.strip >= 0) & \
+        (w.strip < synth.N_Z_STRIPS)
+    cs = np.concatenate([[0], np.cumsum(valid, dtype=np.int64)])
+    hv = cs[w.offsets[1:]] - cs[w.offsets[:-1]]
+    allv = lines.cpu().numpy().view(hough.LINE_DTYPE).reshape(-1)
+    votes = int((hv * (18 + 10 * (allv["coarse_votes"] >= 5))).sum())
+    rate = votes / (ms * 1e-3) / 1e9
     return {"method": "coarse 18x100 then fine 10x10 of the 180x1000 grid, one line per window",
             "ms_per_step": round(ms, 4), "windows_per_s": round(w.n_windows / (ms * 1e-3), 1),
             "windows_with_line": int((lv["found"] == 1).sum()), "compared_windows": n_cmp,
             "same_bin_as_full_top_peak": round(float(same.sum()) / max(int(both.sum()), 1), 4),
-            "within_one_bin": round(float(near.sum()) / max(int(both.sum()), 1), 4)}
+            "within_one_bin": round(float(near.sum()) / max(int(both.sum()), 1), 4),
+            "roofline": {"bound": "alu", "achieved": round(rate, 2), "peak": smem_peak["value"],
+                         "unit": "Gvote/s",
+                         "frac": round(rate / smem_peak["value"], 4) if smem_peak["value"] else None,
+                         "algorithmic": f"{votes} shared-memory votes (18 coarse rows, then 10 "
+                                        "fine rows where the coarse maximum reaches T)"}}
 
 
 def _slicing_leg(args, dev, stream, flush, hbm_gbs):
@@ -785,9 +819,9 @@ def run_ours(args):
         serving = _serving_leg(args, dev) if args.serve_seconds > 0 else None
         slicing = _slicing_leg(args, dev, stream, flush, peaks_meas.get("hbm_gbs")) \
             if args.slice_us > 0 else None
-        coarse_fine = _coarse_fine_leg(args, dev, stream, flush, w, hits, offs) \
+        coarse_fine = _coarse_fine_leg(args, dev, stream, flush, w, hits, offs, smem_peak) \
             if args.coarse_fine else None
-        iterative = _iterative_leg(args, dev, stream, w, hits, offs, out) \
+        iterative = _iterative_leg(args, dev, stream, w, hits, offs, out, smem_peak) \
             if args.iter_windows > 0 else None
         extension = _extension_leg(args, dev, stream, flush, w, hits, offs, out,
                                    peaks_meas.get("hbm_gbs")) if args.extend else None
