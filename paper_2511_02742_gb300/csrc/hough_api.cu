@@ -704,8 +704,14 @@ int hough_find_coarse_fine(hough_ctx *ctx, const hough_hits *hits, const int64_t
     p.tol = ctx->th.assoc_tol_bins;
     p.lines = lines;
     p.hit_track = hit_track;
-    const long long blocks = std::min<long long>(n_windows, (long long)ctx->num_sms * 8);
-    hk::coarse_fine_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(p);
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hk::coarse_fine_kernel,
+                                                      32 * hk::kCfWarps, 0) != cudaSuccess ||
+        occ < 1)
+        return fail(ctx, HOUGH_ERR_CUDA);
+    const long long blocks = std::min<long long>((n_windows + hk::kCfWarps - 1) / hk::kCfWarps,
+                                                 (long long)ctx->num_sms * occ);
+    hk::coarse_fine_kernel<<<(unsigned)blocks, 32 * hk::kCfWarps, 0, (cudaStream_t)stream>>>(p);
     if (cudaGetLastError() != cudaSuccess)
         return fail(ctx, HOUGH_ERR_CUDA);
     ctx->launches += 1;

@@ -9,9 +9,9 @@
 
 namespace hk {
 
-// One CTA per window (grid-stride over windows).  Coarse: every (hit, row)
-// pair of the 18 coarse rows votes into an 18 x 100 shared histogram; a
-// block maximum of (count, -index) gives the coarse bin (ties row-major).
+// Coarse: every (hit, row) pair of the 18 coarse rows votes into an 18 x 100
+// shared histogram; the maximum of (count, -index) gives the coarse bin
+// (ties row-major).
 // Fine: the (hit, row) pairs of the 10 fine rows inside it vote into a 10 x
 // 10 histogram, keeping only the bins of the 10 fine columns; its maximum is
 // the line.  Consecutive threads take the rows of one hit, so the lanes of a
@@ -45,44 +45,43 @@ __device__ __forceinline__ bool cf_load_hit(const CfParams &p, long long i, int 
     return phi >= 0 && (long long)phi < p.phi_end && z >= p.z_min_u && (long long)z <= p.z_end;
 }
 
-// Block maximum of a 64-bit key (all threads get it).
-__device__ __forceinline__ unsigned long long cf_block_max(unsigned long long k,
-                                                           unsigned long long *red)
+// Warp maximum of a 64-bit key (every lane gets it).
+__device__ __forceinline__ unsigned long long cf_warp_max(unsigned long long k)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
         const unsigned long long o = __shfl_xor_sync(0xffffffffu, k, d);
         k = o > k ? o : k;
     }
-    __syncthreads();
-    if (lane == 0)
-        red[warp] = k;
-    __syncthreads();
-    unsigned long long m = 0ull;
-    for (int i = 0; i < nw; ++i)
-        m = red[i] > m ? red[i] : m;
-    return m;
+    return k;
 }
 
-__global__ void __launch_bounds__(256) coarse_fine_kernel(CfParams p)
+// Windows per CTA (one warp each).
+constexpr int kCfWarps = 4;
+
+// One warp per window (grid-stride over windows), with its own coarse and
+// fine histograms in shared memory, so that no phase waits for a block
+// barrier.  The maxima use the key (count << 32) | (2^32 - 1 - index): the
+// highest count, then the first bin in row-major order.
+__global__ void __launch_bounds__(32 * kCfWarps) coarse_fine_kernel(CfParams p)
 {
-    __shared__ int coarse[kCfCoarseT * kCfCoarseR];
-    __shared__ int fine[kCfBlock * kCfBlock];
-    __shared__ unsigned long long red[8];
-    __shared__ int seeds;
-    for (long long w = blockIdx.x; w < p.n_windows; w += gridDim.x) {
+    __shared__ __align__(16) int coarse_s[kCfWarps][kCfCoarseT * kCfCoarseR];
+    __shared__ __align__(16) int fine_s[kCfWarps][kCfBlock * kCfBlock];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int *coarse = coarse_s[warp], *fine = fine_s[warp];
+    const long long n_warps = (long long)gridDim.x * kCfWarps;
+    for (long long w = (long long)blockIdx.x * kCfWarps + warp; w < p.n_windows; w += n_warps) {
         const long long beg = p.offsets[w], end = p.offsets[w + 1];
         const bool ok_off = beg >= 0 && beg <= end && end <= p.n_hits;
         const int H = ok_off ? (int)min(end - beg, (long long)INT_MAX / kCfCoarseT) : 0;
-        for (int i = threadIdx.x; i < kCfCoarseT * kCfCoarseR; i += blockDim.x)
-            coarse[i] = 0;
-        for (int i = threadIdx.x; i < kCfBlock * kCfBlock; i += blockDim.x)
+        int4 *c4 = reinterpret_cast<int4 *>(coarse);
+        for (int i = lane; i < kCfCoarseT * kCfCoarseR / 4; i += 32)
+            c4[i] = make_int4(0, 0, 0, 0);
+        for (int i = lane; i < kCfBlock * kCfBlock; i += 32)
             fine[i] = 0;
-        if (threadIdx.x == 0)
-            seeds = 0;
-        __syncthreads();
-        for (int x = threadIdx.x; x < H * kCfCoarseT; x += blockDim.x) {
+        __syncwarp();
+        // coarse: (hit, row) pairs, consecutive lanes on the rows of one hit
+        for (int x = lane; x < H * kCfCoarseT; x += 32) {
             const int h = x / kCfCoarseT, t = x - h * kCfCoarseT;
             int phi, z;
             if (!cf_load_hit(p, beg + h, phi, z))
@@ -91,21 +90,21 @@ __global__ void __launch_bounds__(256) coarse_fine_kernel(CfParams p)
             if ((unsigned)b < (unsigned)kCfCoarseR)
                 atomicAdd(&coarse[t * kCfCoarseR + b], 1);
         }
-        __syncthreads();
+        __syncwarp();
         unsigned long long key = 0ull;
-        for (int i = threadIdx.x; i < kCfCoarseT * kCfCoarseR; i += blockDim.x) {
+        for (int i = lane; i < kCfCoarseT * kCfCoarseR; i += 32) {
             const unsigned long long k = ((unsigned long long)(unsigned)coarse[i] << 32) |
                                          (unsigned long long)(0xffffffffu - (unsigned)i);
             key = k > key ? k : key;
         }
-        const unsigned long long cmax = cf_block_max(key, red);
+        const unsigned long long cmax = cf_warp_max(key);
         const int cidx = (int)(0xffffffffu - (unsigned)(cmax & 0xffffffffu));
         const int cvotes = (int)(cmax >> 32);
         const int tc = cidx / kCfCoarseR, bc = cidx - tc * kCfCoarseR;
         bool found = cvotes >= p.T;
         int tf = 0, bf = 0, fvotes = 0;
         if (found) {
-            for (int x = threadIdx.x; x < H * kCfBlock; x += blockDim.x) {
+            for (int x = lane; x < H * kCfBlock; x += 32) {
                 const int h = x / kCfBlock, i = x - h * kCfBlock;
                 int phi, z;
                 if (!cf_load_hit(p, beg + h, phi, z))
@@ -116,14 +115,14 @@ __global__ void __launch_bounds__(256) coarse_fine_kernel(CfParams p)
                 if ((unsigned)j < (unsigned)kCfBlock)
                     atomicAdd(&fine[i * kCfBlock + j], 1);
             }
-            __syncthreads();
+            __syncwarp();
             unsigned long long fk = 0ull;
-            for (int i = threadIdx.x; i < kCfBlock * kCfBlock; i += blockDim.x) {
+            for (int i = lane; i < kCfBlock * kCfBlock; i += 32) {
                 const unsigned long long k = ((unsigned long long)(unsigned)fine[i] << 32) |
                                              (unsigned long long)(0xffffffffu - (unsigned)i);
                 fk = k > fk ? k : fk;
             }
-            const unsigned long long fmax = cf_block_max(fk, red);
+            const unsigned long long fmax = cf_warp_max(fk);
             const int fidx = (int)(0xffffffffu - (unsigned)(fmax & 0xffffffffu));
             fvotes = (int)(fmax >> 32);
             tf = tc * kCfBlock + fidx / kCfBlock;
@@ -133,7 +132,7 @@ __global__ void __launch_bounds__(256) coarse_fine_kernel(CfParams p)
         // seeds
         int mine = 0;
         const int cft = __ldg(p.Cf + tf), sft = __ldg(p.Sf + tf);
-        for (int h = threadIdx.x; h < H; h += blockDim.x) {
+        for (int h = lane; h < H; h += 32) {
             int phi, z;
             int v = -2;
             if (cf_load_hit(p, beg + h, phi, z)) {
@@ -151,10 +150,7 @@ __global__ void __launch_bounds__(256) coarse_fine_kernel(CfParams p)
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1)
             mine += __shfl_xor_sync(0xffffffffu, mine, d);
-        if ((threadIdx.x & 31) == 0 && mine)
-            atomicAdd(&seeds, mine);
-        __syncthreads();
-        if (threadIdx.x == 0) {
+        if (lane == 0) {
             hough_line r;
             r.coarse_theta = ok_off ? tc : 0;
             r.coarse_rho = ok_off ? bc : 0;
@@ -162,13 +158,12 @@ __global__ void __launch_bounds__(256) coarse_fine_kernel(CfParams p)
             r.fine_theta = tf;
             r.fine_rho = bf;
             r.fine_votes = fvotes;
-            r.n_seeds = seeds;
+            r.n_seeds = mine;
             r.found = found ? 1 : 0;
             p.lines[w] = r;
         }
-        __syncthreads();
+        __syncwarp();                        // the histograms are cleared next
     }
 }
-
 
 }  // namespace hk
