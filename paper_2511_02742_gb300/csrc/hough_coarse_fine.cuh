@@ -80,15 +80,17 @@ __global__ void __launch_bounds__(32 * kCfWarps) coarse_fine_kernel(CfParams p)
         for (int i = lane; i < kCfBlock * kCfBlock; i += 32)
             fine[i] = 0;
         __syncwarp();
-        // coarse: (hit, row) pairs, consecutive lanes on the rows of one hit
-        for (int x = lane; x < H * kCfCoarseT; x += 32) {
-            const int h = x / kCfCoarseT, t = x - h * kCfCoarseT;
+        // coarse: a lane per hit (loaded and encoded once), over the 18 rows
+        for (int h = lane; h < H; h += 32) {
             int phi, z;
             if (!cf_load_hit(p, beg + h, phi, z))
                 continue;
-            const int b = rho_bin(phi, z, __ldg(p.Cc + t), __ldg(p.Sc + t), p.Dc, p.Kc);
-            if ((unsigned)b < (unsigned)kCfCoarseR)
-                atomicAdd(&coarse[t * kCfCoarseR + b], 1);
+#pragma unroll 6
+            for (int t = 0; t < kCfCoarseT; ++t) {
+                const int b = rho_bin(phi, z, __ldg(p.Cc + t), __ldg(p.Sc + t), p.Dc, p.Kc);
+                if ((unsigned)b < (unsigned)kCfCoarseR)
+                    atomicAdd(&coarse[t * kCfCoarseR + b], 1);
+            }
         }
         __syncwarp();
         unsigned long long key = 0ull;
@@ -104,16 +106,18 @@ __global__ void __launch_bounds__(32 * kCfWarps) coarse_fine_kernel(CfParams p)
         bool found = cvotes >= p.T;
         int tf = 0, bf = 0, fvotes = 0;
         if (found) {
-            for (int x = lane; x < H * kCfBlock; x += 32) {
-                const int h = x / kCfBlock, i = x - h * kCfBlock;
+            for (int h = lane; h < H; h += 32) {
                 int phi, z;
                 if (!cf_load_hit(p, beg + h, phi, z))
                     continue;
-                const int t = tc * kCfBlock + i;
-                const int b = rho_bin(phi, z, __ldg(p.Cf + t), __ldg(p.Sf + t), p.Df, p.Kf);
-                const int j = b - bc * kCfBlock;
-                if ((unsigned)j < (unsigned)kCfBlock)
-                    atomicAdd(&fine[i * kCfBlock + j], 1);
+#pragma unroll 5
+                for (int i = 0; i < kCfBlock; ++i) {
+                    const int t = tc * kCfBlock + i;
+                    const int b = rho_bin(phi, z, __ldg(p.Cf + t), __ldg(p.Sf + t), p.Df, p.Kf);
+                    const int j = b - bc * kCfBlock;
+                    if ((unsigned)j < (unsigned)kCfBlock)
+                        atomicAdd(&fine[i * kCfBlock + j], 1);
+                }
             }
             __syncwarp();
             unsigned long long fk = 0ull;
