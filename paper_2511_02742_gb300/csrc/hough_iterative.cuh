@@ -61,37 +61,6 @@ __device__ int iter_stage(const KParams &p, long long beg, int H, int2 *stage, i
 
 // Highest counter of the voted tile as a key (count << 32 | ~(t << 16 | b)):
 // the block maximum is the highest count, first in row-major order.
-template <int P>
-__device__ unsigned long long tile_best(const KParams &p, const uint32_t *acc, int t0, int R)
-{
-    constexpr int CW = 32 / P;
-    constexpr unsigned MASK = P == 1 ? 0xffffffffu : ((1u << CW) - 1u);
-    const int words = p.word_rows * p.n_rho;
-    unsigned long long best = 0ull;
-    for (int f = threadIdx.x; f < words; f += blockDim.x) {
-        const uint32_t wv = acc[f];
-        if (wv == 0u)
-            continue;
-        const int q = f >> 5;
-        const int g = (int)__umulhi((unsigned)q, p.nrho_inv);
-        const int b = q - g * p.n_rho;
-        const int wr = g * 32 + (f & 31);
-#pragma unroll
-        for (int s = 0; s < P; ++s) {
-            const unsigned v = (wv >> (s * CW)) & MASK;
-            const int i = s * p.word_rows + wr;
-            const int t = t0 + i;
-            if (v != 0u && i < R && t < p.n_theta) {
-                const unsigned long long key = ((unsigned long long)v << 32) |
-                                               (unsigned long long)(0xffffffffu -
-                                                                    (((unsigned)t << 16) | (unsigned)b));
-                best = key > best ? key : best;
-            }
-        }
-    }
-    return best;
-}
-
 __device__ __forceinline__ unsigned long long block_max_u64(unsigned long long k,
                                                             unsigned long long *red)
 {
@@ -109,6 +78,68 @@ __device__ __forceinline__ unsigned long long block_max_u64(unsigned long long k
     for (int i = 0; i < nw; ++i)
         m = red[i] > m ? red[i] : m;
     return m;
+}
+
+// Whether some P-bit field of w equals v (v < 2^(32/P)): the fields of
+// y = w ^ (v in every field) that are zero, by the exact zero-field test
+// (y - 0x..01..01) & ~y & 0x..80..80 (non-zero iff some field of y is zero).
+template <int P>
+__device__ __forceinline__ bool has_field(uint32_t w, unsigned v)
+{
+    if constexpr (P == 1) {
+        return w == v;
+    } else if constexpr (P == 2) {
+        const uint32_t y = w ^ (v * 0x00010001u);
+        return ((y - 0x00010001u) & ~y & 0x80008000u) != 0u;
+    } else {
+        const uint32_t y = w ^ (v * 0x01010101u);
+        return ((y - 0x01010101u) & ~y & 0x80808080u) != 0u;
+    }
+}
+
+// The tile's highest bin as the key (count << 32) | (2^32 - 1 - (t << 16 | b)):
+// the highest count, then the first bin in row-major order.  Two passes over
+// the counters: the highest count (fields only: rows past n_theta never get a
+// vote, so every non-zero field is a bin of the accumulator), then the words
+// holding that count.  Every thread gets the result.
+template <int P>
+__device__ unsigned long long tile_best(const KParams &p, const uint32_t *acc, int t0,
+                                        unsigned long long *red)
+{
+    constexpr int CW = 32 / P;
+    constexpr unsigned MASK = P == 1 ? 0xffffffffu : ((1u << CW) - 1u);
+    const int words = p.word_rows * p.n_rho;
+    unsigned m = 0u;
+    for (int f = threadIdx.x; f < words; f += blockDim.x) {
+        const uint32_t wv = acc[f];
+#pragma unroll
+        for (int s = 0; s < P; ++s)
+            m = max(m, (wv >> (s * CW)) & MASK);
+    }
+    const unsigned top = (unsigned)(block_max_u64(m, red) & 0xffffffffu);
+    if (top == 0u)
+        return 0ull;
+    unsigned long long best = 0ull;
+    for (int f = threadIdx.x; f < words; f += blockDim.x) {
+        const uint32_t wv = acc[f];
+        if (!has_field<P>(wv, top))
+            continue;
+        const int q = f >> 5;
+        const int g = (int)__umulhi((unsigned)q, p.nrho_inv);
+        const int b = q - g * p.n_rho;
+        const int wr = g * 32 + (f & 31);
+#pragma unroll
+        for (int s = 0; s < P; ++s) {
+            if (((wv >> (s * CW)) & MASK) != top)
+                continue;
+            const int t = t0 + s * p.word_rows + wr;
+            const unsigned long long key = ((unsigned long long)top << 32) |
+                                           (unsigned long long)(0xffffffffu -
+                                                                (((unsigned)t << 16) | (unsigned)b));
+            best = key > best ? key : best;
+        }
+    }
+    return block_max_u64(best, red);
 }
 
 // One pass over every tile: the highest bin of the remaining hits' votes.
@@ -132,7 +163,7 @@ __device__ unsigned long long iter_best(const KParams &p, uint32_t *acc, const i
         else
             vote_tile<P, false>(p, acc, stage, nv, t0, nullptr, 0, cnt, none, ws);
         __syncthreads();
-        const unsigned long long k = block_max_u64(tile_best<P>(p, acc, t0, R), red);
+        const unsigned long long k = tile_best<P>(p, acc, t0, red);
         best = k > best ? k : best;
     }
     return best;
