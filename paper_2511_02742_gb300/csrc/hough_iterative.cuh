@@ -143,9 +143,15 @@ __device__ unsigned long long tile_best(const KParams &p, const uint32_t *acc, i
 }
 
 // One pass over every tile: the highest bin of the remaining hits' votes.
+// ub[tile]: an upper bound of the tile's highest count (its highest count
+// when it was last voted: removing hits only lowers counts), valid while the
+// counter width P, and so the tiling, stays the same.  A tile whose bound is
+// below T, or not above the best count of the earlier tiles, cannot hold the
+// highest bin (a later tile wins only with a strictly higher count), so it is
+// not voted.
 template <int P>
 __device__ unsigned long long iter_best(const KParams &p, uint32_t *acc, const int2 *stage, int nv,
-                                        unsigned long long *red, WinScalars &ws)
+                                        unsigned long long *red, WinScalars &ws, int *ub, int T)
 {
     const int R = p.word_rows * P;
     const int n_tiles = (p.n_theta + R - 1) / R;
@@ -153,6 +159,9 @@ __device__ unsigned long long iter_best(const KParams &p, uint32_t *acc, const i
     int cnt = 0;
     const ListOvf none{&ws.n_sel, 0};
     for (int tile = 0; tile < n_tiles; ++tile) {
+        const int bound = ub[tile];
+        if (bound < T || (unsigned long long)(unsigned)bound <= (best >> 32))
+            continue;                        // uniform: ub and best are the block's
         const int t0 = tile * R;
         uint4 *acc4 = reinterpret_cast<uint4 *>(acc);
         for (int i = threadIdx.x; i < (p.word_rows * p.n_rho) >> 2; i += blockDim.x)
@@ -164,6 +173,8 @@ __device__ unsigned long long iter_best(const KParams &p, uint32_t *acc, const i
             vote_tile<P, false>(p, acc, stage, nv, t0, nullptr, 0, cnt, none, ws);
         __syncthreads();
         const unsigned long long k = tile_best<P>(p, acc, t0, red);
+        if (threadIdx.x == 0)
+            ub[tile] = (int)(k >> 32);
         best = k > best ? k : best;
     }
     return best;
@@ -176,6 +187,7 @@ __global__ void __launch_bounds__(512, 1) iterative_kernel(IterParams q)
     __shared__ unsigned long long red[16];
     __shared__ int wtot[32];
     __shared__ int taken;
+    __shared__ int ub[HOUGH_MAX_THETA / 32];      // per-tile bounds (at most n_theta / 32 tiles)
     KParams p = q.k;
     p.T = 0x7fffffff;               // the vote loop lists nothing
     const int T = q.k.T;
@@ -203,14 +215,22 @@ __global__ void __launch_bounds__(512, 1) iterative_kernel(IterParams q)
             flags |= HOUGH_WIN_TOO_LARGE;
             nv = 0;
         }
+        int width = 0;                               // counter fields per word of the bounds
         while (found < q.max_tracks && nv > 0) {
+            const int P = nv <= 255 ? 4 : (nv <= 65535 ? 2 : 1);
+            if (P != width) {                        // new tiling: no bound known yet
+                for (int i = threadIdx.x; i < HOUGH_MAX_THETA / 32; i += blockDim.x)
+                    ub[i] = 0x7fffffff;
+                __syncthreads();
+                width = P;
+            }
             unsigned long long best;
-            if (nv <= 255)
-                best = iter_best<4>(p, acc, stage, nv, red, ws);
-            else if (nv <= 65535)
-                best = iter_best<2>(p, acc, stage, nv, red, ws);
+            if (P == 4)
+                best = iter_best<4>(p, acc, stage, nv, red, ws, ub, T);
+            else if (P == 2)
+                best = iter_best<2>(p, acc, stage, nv, red, ws, ub, T);
             else
-                best = iter_best<1>(p, acc, stage, nv, red, ws);
+                best = iter_best<1>(p, acc, stage, nv, red, ws, ub, T);
             const int votes = (int)(best >> 32);
             if (votes < T)
                 break;
