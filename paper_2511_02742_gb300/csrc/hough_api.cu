@@ -730,8 +730,9 @@ int hough_find_iterative(hough_ctx *ctx, const hough_hits *hits, const int64_t *
         return fail(ctx, HOUGH_ERR_INVALID_ARG);
     if (n_windows == 0)
         return HOUGH_OK;
-    // 512 threads, the largest tile that fits beside the stage of hits and
-    // the kernel's static shared variables
+    // 512 threads, tiles of 32 word rows beside the stage of hits and the
+    // kernel's static shared variables (small tiles let more of them be
+    // skipped once their count bound falls; 64 or 128 word rows were slower)
     hough_launch l{512, 32, HOUGH_ITER_MAX_HITS, 1};
     const size_t stage = (size_t)HOUGH_ITER_MAX_HITS * 12;
     cudaFuncAttributes fa{};
@@ -739,12 +740,6 @@ int hough_find_iterative(hough_ctx *ctx, const hough_hits *hits, const int64_t *
         return fail(ctx, HOUGH_ERR_CUDA);
     const size_t room = ctx->smem_optin + 128 > fa.sharedSizeBytes
                             ? ctx->smem_optin + 128 - fa.sharedSizeBytes : 0;
-    for (int wr : {128, 64}) {
-        if ((size_t)wr * ctx->n_rho * 4 + stage <= room && ctx->n_theta >= 2 * wr) {
-            l.word_rows = wr;
-            break;
-        }
-    }
     const size_t smem = (size_t)l.word_rows * ctx->n_rho * 4 + stage;
     if (smem > room)
         return fail(ctx, HOUGH_ERR_UNSUPPORTED_SHAPE);
