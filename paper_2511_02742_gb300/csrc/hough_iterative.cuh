@@ -145,23 +145,49 @@ __device__ unsigned long long tile_best(const KParams &p, const uint32_t *acc, i
 // One pass over every tile: the highest bin of the remaining hits' votes.
 // ub[tile]: an upper bound of the tile's highest count (its highest count
 // when it was last voted: removing hits only lowers counts), valid while the
-// counter width P, and so the tiling, stays the same.  A tile whose bound is
-// below T, or not above the best count of the earlier tiles, cannot hold the
-// highest bin (a later tile wins only with a strictly higher count), so it is
-// not voted.
+// counter width P, and so the tiling, stays the same.  The tiles are taken in
+// decreasing order of their bound (ties: the earlier tile first), so that the
+// best count is found early; a tile is voted only if it could still hold the
+// highest bin: a bound of at least T and above the best count so far, or
+// equal to it in a tile before the best bin's (the first bin in row-major
+// order wins a tie).  done: one bit per tile, this call's visits.
 template <int P>
 __device__ unsigned long long iter_best(const KParams &p, uint32_t *acc, const int2 *stage, int nv,
-                                        unsigned long long *red, WinScalars &ws, int *ub, int T)
+                                        unsigned long long *red, WinScalars &ws, int *ub,
+                                        unsigned *done, int T)
 {
     const int R = p.word_rows * P;
     const int n_tiles = (p.n_theta + R - 1) / R;
+    const int lane = threadIdx.x & 31;
     unsigned long long best = 0ull;
+    int best_tile = n_tiles;
     int cnt = 0;
     const ListOvf none{&ws.n_sel, 0};
-    for (int tile = 0; tile < n_tiles; ++tile) {
-        const int bound = ub[tile];
-        if (bound < T || (unsigned long long)(unsigned)bound <= (best >> 32))
-            continue;                        // uniform: ub and best are the block's
+    for (int i = threadIdx.x; i < (n_tiles + 31) / 32; i += blockDim.x)
+        done[i] = 0u;
+    __syncthreads();
+    for (;;) {
+        // every warp picks the same tile: the largest (bound, -index) not yet visited
+        unsigned long long pick = 0ull;
+        for (int x = lane; x < n_tiles; x += 32) {
+            if ((done[x >> 5] >> (x & 31)) & 1u)
+                continue;
+            const unsigned long long k = ((unsigned long long)(unsigned)ub[x] << 32) |
+                                         (unsigned long long)(0xffffffffu - (unsigned)x);
+            pick = k > pick ? k : pick;
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, pick, d);
+            pick = o > pick ? o : pick;
+        }
+        if (pick == 0ull)
+            break;                                   // every tile visited
+        const int tile = (int)(0xffffffffu - (unsigned)(pick & 0xffffffffu));
+        const unsigned bound = (unsigned)(pick >> 32);
+        const unsigned top = (unsigned)(best >> 32);
+        if ((int)bound < T || bound < top || (bound == top && tile > best_tile))
+            break;                                   // no unvisited tile can hold the highest bin
         const int t0 = tile * R;
         uint4 *acc4 = reinterpret_cast<uint4 *>(acc);
         for (int i = threadIdx.x; i < (p.word_rows * p.n_rho) >> 2; i += blockDim.x)
@@ -173,9 +199,15 @@ __device__ unsigned long long iter_best(const KParams &p, uint32_t *acc, const i
             vote_tile<P, false>(p, acc, stage, nv, t0, nullptr, 0, cnt, none, ws);
         __syncthreads();
         const unsigned long long k = tile_best<P>(p, acc, t0, red);
-        if (threadIdx.x == 0)
+        if (threadIdx.x == 0) {
             ub[tile] = (int)(k >> 32);
-        best = k > best ? k : best;
+            done[tile >> 5] |= 1u << (tile & 31);
+        }
+        if (k > best) {
+            best = k;
+            best_tile = tile;
+        }
+        __syncthreads();
     }
     return best;
 }
@@ -188,6 +220,7 @@ __global__ void __launch_bounds__(512, 1) iterative_kernel(IterParams q)
     __shared__ int wtot[32];
     __shared__ int taken;
     __shared__ int ub[HOUGH_MAX_THETA / 32];      // per-tile bounds (at most n_theta / 32 tiles)
+    __shared__ unsigned done[HOUGH_MAX_THETA / 32 / 32];
     KParams p = q.k;
     p.T = 0x7fffffff;               // the vote loop lists nothing
     const int T = q.k.T;
@@ -226,11 +259,11 @@ __global__ void __launch_bounds__(512, 1) iterative_kernel(IterParams q)
             }
             unsigned long long best;
             if (P == 4)
-                best = iter_best<4>(p, acc, stage, nv, red, ws, ub, T);
+                best = iter_best<4>(p, acc, stage, nv, red, ws, ub, done, T);
             else if (P == 2)
-                best = iter_best<2>(p, acc, stage, nv, red, ws, ub, T);
+                best = iter_best<2>(p, acc, stage, nv, red, ws, ub, done, T);
             else
-                best = iter_best<1>(p, acc, stage, nv, red, ws, ub, T);
+                best = iter_best<1>(p, acc, stage, nv, red, ws, ub, done, T);
             const int votes = (int)(best >> 32);
             if (votes < T)
                 break;
