@@ -47,3 +47,27 @@ def test_uneven_windows_other_shapes_and_truncation(hough):
     _check(hough, w, 512, 512)
     _check(hough, w, 180, 1000, max_tracks=3)
     _check(hough, synth.workload("high_pileup", n_windows=4, seed=33), 1024, 1024)
+
+
+@pytest.mark.parametrize("th1,r1,th2,r2", [(30, 0, 120, -175), (60, -100, 150, -200),
+                                           (20, 50, 100, -200), (70, -125, 110, -200)])
+def test_equal_lines_in_different_tiles(hough, th1, r1, th2, r2):
+    """Two lines of 12 hits each whose highest bins lie in different theta
+    tiles with equal counts: the first bin in row-major order is taken first,
+    whatever order the tiles are visited in; a third, shorter line and noise
+    around them."""
+    a = synth.line_window(th1, r1, vanes=range(0, 12))
+    b = synth.line_window(th2, r2, vanes=range(20, 32))
+    c = synth.line_window(90.0, 30.0, vanes=range(33, 39))
+    rng = np.random.default_rng(th1)
+    noise_v = rng.integers(0, 40, 8).astype(np.int32)
+    noise_s = rng.integers(0, 2048, 8).astype(np.int32)
+    for order in (0, 1):
+        parts = [(a.vane, a.strip), (b.vane, b.strip)][::1 if order == 0 else -1]
+        vane = np.concatenate([parts[0][0], parts[1][0], c.vane, noise_v])
+        strip = np.concatenate([parts[0][1], parts[1][1], c.strip, noise_s])
+        w = synth.Windows(vane, strip, np.array([0, len(vane)], np.int64),
+                          np.zeros(len(vane), np.int32), np.zeros(len(vane)), np.zeros((1, 4)),
+                          np.array([0, 1], np.int64))
+        _check(hough, w, 512, 512)
+        _check(hough, w, 1024, 1024)
