@@ -330,3 +330,33 @@ def test_export_to_an_unaligned_accumulator(hough):
     np.testing.assert_array_equal(out["acc"].cpu().numpy(), a["acc"].cpu().numpy())
     assert int(buf[0].item()) == -5
     f.close()
+
+
+@pytest.mark.parametrize("shift_a,shift_b", [(0, 0), (1, 1), (2, 3), (0, 1)])
+def test_hit_arrays_at_any_alignment(hough, shift_a, shift_b):
+    """Windows of 0 to about 80 hits starting at every residue mod 4, with the
+    hit arrays 16-byte aligned or shifted by 4 to 12 bytes (each array on its
+    own): every window equals the oracle's, for encoded hits and raw ones."""
+    import torch
+    rng = np.random.default_rng(77)
+    parts = [synth.generate(1, int(rng.integers(0, 4)), (100.0, 300.0), float(rng.uniform(0, 0.05)),
+                            seed=700 + k) for k in range(160)]
+    w = synth.concat(parts)
+    n = np.diff(w.offsets)
+    assert set(w.offsets[:-1][n >= 8] % 4) == {0, 1, 2, 3} and (n == 0).any() and (n < 4).any()
+    f = _finder(hough, 256, 256)
+    phi, z = oracle.encode(f.geometry, w.vane, w.strip)
+    ref = oracle_run(w, 256, 256)
+    for raw in (True, False):
+        a, b = (w.vane, w.strip) if raw else (phi, z)
+        ta = torch.zeros(len(a) + 4, dtype=torch.int32, device="cuda")
+        tb = torch.zeros(len(b) + 4, dtype=torch.int32, device="cuda")
+        va, vb = ta[shift_a:shift_a + len(a)], tb[shift_b:shift_b + len(b)]
+        va.copy_(torch.from_numpy(a))
+        vb.copy_(torch.from_numpy(b))
+        assert va.data_ptr() % 16 == 4 * shift_a and vb.data_ptr() % 16 == 4 * shift_b
+        hits = dict(vane=va, strip=vb) if raw else dict(phi_q=va, z_q=vb)
+        out = f.find(hits, torch.from_numpy(w.offsets).cuda())
+        torch.cuda.synchronize()
+        assert_batch_equal(to_numpy(out, w.n_hits), ref, w)
+    f.close()

@@ -162,3 +162,31 @@ def test_binding_structs_match_the_header(tmp_path):
             assert int(got[f"{n} {field}"]) == getattr(st, field).offset, (n, field)
     assert int(got["hough_peak size"]) == hough.PEAK_DTYPE.itemsize == 16
     assert int(got["hough_ext_track size"]) == hough.EXT_DTYPE.itemsize == 16
+
+
+def test_binding_constants_match_the_header(tmp_path):
+    """Every HOUGH_* integer constant of the binding has the value the C
+    compiler gives the macro of the same name in include/hough.h, and every
+    per-window flag and limit macro of the header has a binding constant."""
+    import subprocess
+    from paper_2511_02742_gb300 import hough
+    src_h = open(os.path.join(ROOT, "include", "hough.h")).read()
+    macros = re.findall(r"^#define\s+(HOUGH_\w+)\s+\S", src_h, flags=re.M)
+    ours = {n: getattr(hough, n) for n in dir(hough) if n.startswith("HOUGH_")
+            and isinstance(getattr(hough, n), int)}
+    for n in macros:
+        if n.startswith(("HOUGH_WIN_", "HOUGH_MAX_", "HOUGH_FLAG_")):
+            assert n in ours, n
+    names = sorted(set(macros) & set(ours))
+    lines = ['#include <stdio.h>', '#include "hough.h"', 'int main(void) {']
+    lines += [f'printf("{n} %lld\\n", (long long)({n}));' for n in names]
+    lines += ['return 0;', '}']
+    (tmp_path / "consts.c").write_text("\n".join(lines))
+    exe = tmp_path / "consts"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe),
+                    str(tmp_path / "consts.c")], check=True)
+    got = dict(line.split() for line in
+               subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines())
+    assert len(names) >= 10
+    for n in names:
+        assert int(got[n]) == ours[n], n
