@@ -262,6 +262,26 @@ int hough_find_coarse_fine(hough_ctx *ctx, const hough_hits *hits, const int64_t
                            void *stream);
 
 /*
+ * Steps A-B with the histograms written out: for every window, the full
+ * n_theta x n_rho accumulator of Eq. (1) with the Section 5 binning (each
+ * valid hit votes once in each theta row), exactly the accumulator that
+ * hough_find writes with HOUGH_FLAG_EXPORT_ACC, without steps C-D.
+ *   acc[n_windows * n_theta * n_rho]  device int32, row-major per window;
+ *                                     any 4-byte alignment (16-byte aligned
+ *                                     is written with 16-byte stores);
+ *   window_status[n_windows]          device, HOUGH_WIN_HIT_OUT_OF_RANGE,
+ *                                     HOUGH_WIN_VOTE_OUT_OF_RANGE, or
+ *                                     HOUGH_WIN_BAD_OFFSETS (that window's
+ *                                     accumulator is not written).
+ * Hits and offsets as hough_find; fixed-point contexts only (an FP64
+ * context gives INVALID_ARG).  Both buffers are the caller's.  Asynchronous
+ * on stream.
+ * Errors: INVALID_ARG, UNSUPPORTED_SHAPE, CUDA.
+ */
+int hough_accumulate(hough_ctx *ctx, const hough_hits *hits, const int64_t *window_offsets,
+                     int64_t n_windows, int32_t *acc, uint32_t *window_status, void *stream);
+
+/*
  * Iterative highest-bin search (the literal reading of the paper's peak step,
  * Section 4: the bin with the highest accumulation is the most probable
  * line, Section 5: its seeds are the hits aligned with it; repeated until no

@@ -21,6 +21,7 @@ DEPS = [SRC, SERVER_SRC, os.path.join(PKG, "csrc", "hough_kernels.cuh"),
         os.path.join(PKG, "csrc", "hough_iterative.cuh"),
         os.path.join(PKG, "csrc", "hough_extend.cuh"),
         os.path.join(PKG, "csrc", "hough_slice.cuh"),
+        os.path.join(PKG, "csrc", "hough_accumulate.cuh"),
         os.path.join(ROOT, "include", "hough.h")]
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libhough.so")

@@ -23,6 +23,7 @@
 #include "hough_iterative.cuh"
 #include "hough_extend.cuh"
 #include "hough_slice.cuh"
+#include "hough_accumulate.cuh"
 
 // Whether every valid hit votes inside [0, n_rho) in every row: the bin is
 // monotone in phi and in z, so the four corners of the detector box bound it.
@@ -712,6 +713,52 @@ int hough_find_coarse_fine(hough_ctx *ctx, const hough_hits *hits, const int64_t
     const long long blocks = std::min<long long>((n_windows + hk::kCfWarps - 1) / hk::kCfWarps,
                                                  (long long)ctx->num_sms * occ);
     hk::coarse_fine_kernel<<<(unsigned)blocks, 32 * hk::kCfWarps, 0, (cudaStream_t)stream>>>(p);
+    if (cudaGetLastError() != cudaSuccess)
+        return fail(ctx, HOUGH_ERR_CUDA);
+    ctx->launches += 1;
+    return HOUGH_OK;
+}
+
+int hough_accumulate(hough_ctx *ctx, const hough_hits *hits, const int64_t *window_offsets,
+                     int64_t n_windows, int32_t *acc, uint32_t *window_status, void *stream)
+{
+    if (!ctx || !hits_ok(hits) || n_windows < 0 || n_windows >= (1ll << 31) - 65536 ||
+        (n_windows > 0 && (!window_offsets || !acc || !window_status)) ||
+        (reinterpret_cast<uintptr_t>(acc) & 3u) != 0 || (ctx->th.flags & HOUGH_FLAG_FP64))
+        return fail(ctx, HOUGH_ERR_INVALID_ARG);
+    if (n_windows == 0)
+        return HOUGH_OK;
+    // tiles of 32 word rows and a stage of 2048 hits; 512-thread CTAs where
+    // two or more fit on an SM, else one CTA of 1024 threads
+    const int word_rows = 32, hit_stage = 2048;
+    const size_t smem = hk::align_up((size_t)word_rows * ctx->n_rho * 4, 16) + (size_t)hit_stage * 8;
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, hk::accumulate_kernel) != cudaSuccess)
+        return fail(ctx, HOUGH_ERR_CUDA);
+    if (smem + fa.sharedSizeBytes > ctx->smem_optin)
+        return fail(ctx, HOUGH_ERR_UNSUPPORTED_SHAPE);
+    if (cudaFuncSetAttribute(hk::accumulate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return fail(ctx, HOUGH_ERR_CUDA);
+    int threads = 512, occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hk::accumulate_kernel, threads, smem) !=
+        cudaSuccess)
+        return fail(ctx, HOUGH_ERR_CUDA);
+    if (occ < 2) {
+        threads = 1024;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hk::accumulate_kernel, threads,
+                                                          smem) != cudaSuccess)
+            return fail(ctx, HOUGH_ERR_CUDA);
+        if (occ < 1)
+            return fail(ctx, HOUGH_ERR_UNSUPPORTED_SHAPE);
+    }
+    hough_tracks out{};
+    out.acc = acc;
+    out.window_status = window_status;
+    hough_launch l{threads, word_rows, hit_stage, occ};
+    const hk::KParams p = make_params(ctx, hits, window_offsets, n_windows, &out, nullptr, l);
+    const long long grid = std::min<long long>(n_windows, (long long)ctx->num_sms * occ);
+    hk::accumulate_kernel<<<(unsigned)grid, threads, smem, (cudaStream_t)stream>>>(p);
     if (cudaGetLastError() != cudaSuccess)
         return fail(ctx, HOUGH_ERR_CUDA);
     ctx->launches += 1;

@@ -148,6 +148,7 @@ def load(build_if_missing: bool = False):
         "hough_launch_count": ([P], i64),
         "hough_find_coarse_fine": ([P, P, P, i64, P, P, P], i32),
         "hough_find_iterative": ([P, P, P, i64, ctypes.c_int32, P, P, P, P, P], i32),
+        "hough_accumulate": ([P, P, P, i64, P, P, P], i32),
         "hough_time_slice": ([P, P, P, P, i64, i64, i64, i64, i64, P, P, P, i64, P, P, P], i32),
         "hough_extend": ([P, P, P, i64, P, ctypes.c_int32, P, P], i32),
         "hough_server_create": ([P, P, P], i32),
@@ -324,6 +325,15 @@ def hough_find_coarse_fine(ctx, hits: hough_hits, window_offsets, n_windows: int
     _check(load().hough_find_coarse_fine(ctx, ctypes.byref(hits), _ptr(window_offsets), n_windows,
                                          _ptr(lines), _ptr(hit_track), _stream(stream)),
            "hough_find_coarse_fine")
+
+
+def hough_accumulate(ctx, hits: hough_hits, window_offsets, n_windows: int, acc, window_status,
+                     stream=None) -> None:
+    """Steps A-B with every window's accumulator written out;
+    acc: int32 tensor [n_windows, n_theta, n_rho]."""
+    _check(load().hough_accumulate(ctx, ctypes.byref(hits), _ptr(window_offsets), int(n_windows),
+                                   _ptr(acc), _ptr(window_status), _stream(stream)),
+           "hough_accumulate")
 
 
 ITER_DTYPE = np.dtype([(k, "<i4") for k in ("theta", "rho", "votes", "n_hits")])
@@ -511,6 +521,24 @@ class Finder:
     def find(self, hits: dict, offsets, out: dict | None = None, stream=None) -> dict:
         n_windows, _, out = self._checked(hits, offsets, out, cuda=True)
         hough_find(self.ctx, self.hits_struct(hits), offsets, n_windows, make_tracks(out), stream)
+        return out
+
+    def accumulate(self, hits: dict, offsets, out: dict | None = None, stream=None) -> dict:
+        """Every window's full accumulator (hough_accumulate), no peaks:
+        out = dict(acc [n_windows, n_theta, n_rho], window_status [n_windows])."""
+        import torch
+        n_hits = _check_hits(hits, True)
+        _check_buf(offsets, torch.int64, 1, True, "offsets")
+        n_windows = int(offsets.numel()) - 1
+        if out is None:
+            out = dict(acc=torch.empty((n_windows, self.n_theta, self.n_rho), dtype=torch.int32,
+                                       device="cuda"),
+                       window_status=torch.zeros(max(n_windows, 1), dtype=torch.int32,
+                                                 device="cuda"))
+        _check_buf(out["acc"], torch.int32, n_windows * self.n_theta * self.n_rho, True, "acc")
+        _check_buf(out["window_status"], torch.int32, n_windows, True, "window_status")
+        hough_accumulate(self.ctx, self.hits_struct(hits), offsets, n_windows, out["acc"],
+                         out["window_status"], stream)
         return out
 
     def find_host(self, hits: dict, offsets, out: dict | None = None, stream=None) -> dict:

@@ -101,6 +101,7 @@ def test_null_pointers_are_rejected(lib):
     assert lib.hough_encode(None, None, None, 0, None, None, None) == -1
     assert lib.hough_find_coarse_fine(None, None, None, 0, None, None, None) == -1
     assert lib.hough_find_iterative(None, None, None, 0, 1, None, None, None, None, None) == -1
+    assert lib.hough_accumulate(None, None, None, 0, None, None, None) == -1
     assert lib.hough_extend(None, None, None, 0, None, 0, None, None) == -1
     assert lib.hough_time_slice(None, None, None, None, 0, 0, 5, 10, 1, None, None, None, 0,
                                 None, None, None) == -1
