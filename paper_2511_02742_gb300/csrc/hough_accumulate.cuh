@@ -73,6 +73,7 @@ __device__ void export_tile_rows(const KParams &p, uint32_t *acc, int t0, int R,
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int nblk = p.n_rho >> 5;
     int32_t *out = p.acc + (size_t)w * p.n_theta * p.n_rho;
+    const bool full = t0 + R <= p.n_theta;
     for (int item = warp; item < G * nblk; item += nw) {
         const int g = item / nblk, b0 = (item - g * nblk) * 32;
         uint32_t *blk = acc + (size_t)(g * p.n_rho + b0) * 32;
@@ -85,14 +86,30 @@ __device__ void export_tile_rows(const KParams &p, uint32_t *acc, int t0, int R,
         for (int j = 0; j < 32; ++j)
             blk[lane * 32 + (j ^ lane)] = r[j];
         __syncwarp();
-#pragma unroll 4
-        for (int q = 0; q < 32; ++q) {
-            const uint32_t v = blk[q * 32 + (lane ^ q)];    // word (g*32 + q, b0 + lane)
+        if (full) {
+            // every theta row of the tile exists: row g*32 + q + s*WR of the
+            // tile is output row t0 + g*32 + q + s*WR, at a 32-bit offset
+            int32_t *o = out + (size_t)(t0 + g * 32) * p.n_rho + b0 + lane;
+            const int sstep = WR * p.n_rho;
+            int off = 0;
+#pragma unroll 8
+            for (int q = 0; q < 32; ++q) {
+                const uint32_t v = blk[q * 32 + (lane ^ q)];    // word (g*32 + q, b0 + lane)
 #pragma unroll
-            for (int s = 0; s < P; ++s) {
-                const int i = s * WR + g * 32 + q, t = t0 + i;
-                if (i < R && t < p.n_theta)
-                    out[(size_t)t * p.n_rho + b0 + lane] = (int)((v >> (s * CW)) & MASK);
+                for (int s = 0; s < P; ++s)
+                    o[off + s * sstep] = (int)((v >> (s * CW)) & MASK);
+                off += p.n_rho;
+            }
+        } else {
+#pragma unroll 4
+            for (int q = 0; q < 32; ++q) {
+                const uint32_t v = blk[q * 32 + (lane ^ q)];
+#pragma unroll
+                for (int s = 0; s < P; ++s) {
+                    const int i = s * WR + g * 32 + q, t = t0 + i;
+                    if (i < R && t < p.n_theta)
+                        out[(size_t)t * p.n_rho + b0 + lane] = (int)((v >> (s * CW)) & MASK);
+                }
             }
         }
     }
