@@ -50,3 +50,33 @@ def test_host_buffer_checks():
             hough._check_host(bad, np.int32, 1, "c")
     with pytest.raises(ValueError):
         hough._check_host(np.zeros(2, np.int32), np.int32, 3, "d")
+
+
+def test_accumulate_checks_before_any_call():
+    """Finder.accumulate refuses host hits and an accumulator too small for
+    n_windows x n_theta x n_rho before it reaches the library."""
+    import types
+    stub = types.SimpleNamespace(n_theta=4, n_rho=8, ctx=None)
+    v = torch.zeros(5, dtype=torch.int32)
+    offs = torch.tensor([0, 2, 5], dtype=torch.int64)
+    with pytest.raises(ValueError):
+        hough.Finder.accumulate(stub, dict(vane=v, strip=v), offs)
+    orig = hough._check_hits
+    try:
+        hough._check_hits = lambda hits, cuda: 5           # pretend the hits are on the GPU
+        orig_buf = hough._check_buf
+        seen = []
+
+        def check_buf(x, dtype, n, cuda, name):
+            seen.append((name, n))
+            if name != "offsets":
+                orig_buf(x, dtype, n, False, name)
+        hough._check_buf = check_buf
+        small = dict(acc=torch.zeros(2 * 4 * 8 - 1, dtype=torch.int32),
+                     window_status=torch.zeros(2, dtype=torch.int32))
+        with pytest.raises(ValueError):
+            hough.Finder.accumulate(stub, dict(vane=v, strip=v), offs, out=small)
+        assert ("acc", 2 * 4 * 8) in seen
+    finally:
+        hough._check_hits = orig
+        hough._check_buf = orig_buf
