@@ -59,11 +59,24 @@ __device__ void acc_vote_tile(const KParams &p, uint32_t *acc, const int2 *stage
 
 // Export of a tile that is not read again: each warp takes a block of 32
 // word rows x 32 bins (1024 consecutive words of the bank-private layout),
-// holds it in registers, writes it back transposed in place (XOR-swizzled,
-// so both the write and the read that follows are conflict-free), and then
-// writes each word row's P theta rows as 32 consecutive bins (one 128-byte
-// line per store).  Bins past the last whole block of 32 (n_rho not a
-// multiple of 32) go out one lane per word row with 4-byte stores.
+// holds it in registers and writes it back transposed in place: word row r
+// becomes 32 consecutive words (bins b0..b0+31), its 16-byte chunk c stored
+// at chunk c ^ (r & 7), so that the 16-byte writes and reads that follow
+// take the minimum four wavefronts.  Each lane then reads four bins of one
+// word row and writes each of its P theta rows with one 16-byte store: a
+// warp store covers four whole 128-byte lines.  Bins past the last whole
+// block of 32 (n_rho not a multiple of 32) go out one lane per word row
+// with 4-byte stores, as does everything when the accumulator is not
+// 16-byte aligned or the tile has rows past n_theta (then row by row).
+template <int P>
+__device__ __forceinline__ int4 fields4(const uint4 &v, int s)
+{
+    constexpr int CW = 32 / P;
+    constexpr unsigned MASK = P == 1 ? 0xffffffffu : ((1u << CW) - 1u);
+    return make_int4((int)((v.x >> (s * CW)) & MASK), (int)((v.y >> (s * CW)) & MASK),
+                     (int)((v.z >> (s * CW)) & MASK), (int)((v.w >> (s * CW)) & MASK));
+}
+
 template <int P>
 __device__ void export_tile_rows(const KParams &p, uint32_t *acc, int t0, int R, long long w)
 {
@@ -73,7 +86,7 @@ __device__ void export_tile_rows(const KParams &p, uint32_t *acc, int t0, int R,
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int nblk = p.n_rho >> 5;
     int32_t *out = p.acc + (size_t)w * p.n_theta * p.n_rho;
-    const bool full = t0 + R <= p.n_theta;
+    const bool fast = t0 + R <= p.n_theta && (reinterpret_cast<uintptr_t>(p.acc) & 15u) == 0u;
     for (int item = warp; item < G * nblk; item += nw) {
         const int g = item / nblk, b0 = (item - g * nblk) * 32;
         uint32_t *blk = acc + (size_t)(g * p.n_rho + b0) * 32;
@@ -83,27 +96,26 @@ __device__ void export_tile_rows(const KParams &p, uint32_t *acc, int t0, int R,
             r[j] = blk[j * 32 + lane];                 // word (g*32 + lane, b0 + j)
         __syncwarp();
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-            blk[lane * 32 + (j ^ lane)] = r[j];
+        for (int c = 0; c < 8; ++c)
+            *reinterpret_cast<uint4 *>(blk + lane * 32 + ((c ^ (lane & 7)) << 2)) =
+                make_uint4(r[4 * c], r[4 * c + 1], r[4 * c + 2], r[4 * c + 3]);
         __syncwarp();
-        if (full) {
-            // every theta row of the tile exists: row g*32 + q + s*WR of the
-            // tile is output row t0 + g*32 + q + s*WR, at a 32-bit offset
-            int32_t *o = out + (size_t)(t0 + g * 32) * p.n_rho + b0 + lane;
+        if (fast) {
+            // lane: word row q + (lane >> 3), bins b0 + 4 (lane & 7) .. + 3
+            const int rs = lane >> 3, c = lane & 7;
+            int32_t *o = out + (size_t)(t0 + g * 32 + rs) * p.n_rho + b0 + 4 * c;
             const int sstep = WR * p.n_rho;
-            int off = 0;
-#pragma unroll 8
-            for (int q = 0; q < 32; ++q) {
-                const uint32_t v = blk[q * 32 + (lane ^ q)];    // word (g*32 + q, b0 + lane)
+#pragma unroll 4
+            for (int q = 0; q < 32; q += 4) {
+                const int row = q + rs;
+                const uint4 v = *reinterpret_cast<const uint4 *>(blk + row * 32 + ((c ^ (row & 7)) << 2));
 #pragma unroll
                 for (int s = 0; s < P; ++s)
-                    o[off + s * sstep] = (int)((v >> (s * CW)) & MASK);
-                off += p.n_rho;
+                    *reinterpret_cast<int4 *>(o + q * p.n_rho + s * sstep) = fields4<P>(v, s);
             }
         } else {
-#pragma unroll 4
             for (int q = 0; q < 32; ++q) {
-                const uint32_t v = blk[q * 32 + (lane ^ q)];
+                const uint32_t v = blk[q * 32 + ((((lane >> 2) ^ (q & 7))) << 2) + (lane & 3)];
 #pragma unroll
                 for (int s = 0; s < P; ++s) {
                     const int i = s * WR + g * 32 + q, t = t0 + i;
