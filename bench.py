@@ -911,15 +911,22 @@ def run_ours(args):
 
 
 def _smem_atomic_peak_gops(args):
-    """Shared-memory atomic throughput measured by the probe kernel (conflict-free
-    32-bit atomicAdd, all SMs), or the unit-count figure if the probe is off."""
+    """Shared-memory atomic throughput measured by the bench-side probe
+    (conflict-free 32-bit adds, all SMs), or the unit-count figure if the probe
+    is off.  The ceiling is the form the vote loop issues: atom.shared.add with
+    the returned old value consumed; the no-return red.shared.add is measured
+    beside it."""
     nominal = 152 * 32 * 2.070   # SMs x banks x GHz: one 32-lane wavefront per clock per SM
     if args.no_probe:
         return {"value": round(nominal, 1), "source": "nominal: 152 SMs x 32 banks x 2.07 GHz"}
     try:
-        from paper_2511_02742_gb300 import probe
-        v = probe.smem_atomic_gops()
-        return {"value": round(v, 1), "source": "measured: conflict-free smem atomicAdd probe"}
+        import bench_probe
+        v = bench_probe.smem_atomic_gops("atom")
+        r = bench_probe.smem_atomic_gops("red")
+        return {"value": round(v, 1),
+                "source": "measured: conflict-free atom.shared.add.u32 with the returned value "
+                          "consumed (the vote loop's op), bench_probe",
+                "red_no_return_gops": round(r, 1)}
     except Exception as e:  # pragma: no cover
         return {"value": round(nominal, 1), "source": f"nominal (probe failed: {e})"}
 

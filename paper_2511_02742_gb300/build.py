@@ -61,27 +61,6 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     return LIB
 
 
-PROBE_SRC = os.path.join(PKG, "csrc", "probe.cu")
-PROBE_LIB = os.path.join(OUT_DIR, "libhough_probe.so")
-
-
-def build_probe(force: bool = False) -> str:
-    """The shared-atomic throughput probe used as the vote loop's roofline."""
-    if not force and os.path.exists(PROBE_LIB) and \
-            os.path.getmtime(PROBE_LIB) >= os.path.getmtime(PROBE_SRC):
-        return PROBE_LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
-    tmp = PROBE_LIB + f".{os.getpid()}.tmp"
-    res = subprocess.run([nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-                          "-shared", "-o", tmp, PROBE_SRC], capture_output=True, text=True)
-    if res.returncode != 0:
-        sys.stderr.write(res.stdout + res.stderr)
-        raise RuntimeError("nvcc failed building the probe")
-    os.replace(tmp, PROBE_LIB)
-    return PROBE_LIB
-
-
 if __name__ == "__main__":
     build(force=True, verbose="-v" in sys.argv)
-    build_probe(force=True)
     print(LIB)

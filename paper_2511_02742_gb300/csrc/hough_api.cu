@@ -252,15 +252,12 @@ hk::KParams make_params(const hough_ctx *ctx, const hough_hits *hits, const int6
                             (unsigned long long)ctx->n_rho);
     p.hit_stage = l.hit_stage;
     p.kp = std::max(32, next_pow2(std::max(1, ctx->th.max_peaks)));
-    // the list area: a sixth (at least one entry per thread) for the
-    // gathered entries of the check (larger lists are gathered in rounds),
-    // the rest split into per-warp lists, half of each (a multiple of 32)
-    // being the warp's overflow area: a lane's column overflows when its
-    // word row is crossed by many more lines than the average row
+    // the list area, split into per-warp lists (a multiple of 32 entries),
+    // half of each being the warp's overflow area: a lane's column overflows
+    // when its word row is crossed by many more lines than the average row
     const int cl = cl_entries_for(ctx, l.word_rows, l.hit_stage, l.ctas_per_sm, l.threads);
     p.cl_total = cl;
-    p.cmp_cap = std::max(l.threads, cl / 6 / l.threads * l.threads);
-    p.seg_cl = (cl - p.cmp_cap) / (l.threads / 32);
+    p.seg_cl = (cl / (l.threads / 32)) & ~31;
     p.seg_ovf = (p.seg_cl / 2) & ~31;
     return p;
 }

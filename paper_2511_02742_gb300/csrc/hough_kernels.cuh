@@ -96,7 +96,6 @@ struct KParams {
     int cl_total;       // entries of the list area (the host sized shared memory with it)
     int seg_cl;         // candidate-list entries per warp
     int seg_ovf;        // of which the warp's shared overflow area
-    int cmp_cap;        // gathered-entry area after the lists (a multiple of blockDim)
 };
 
 // Shared-memory carve-up shared by host (size) and device (pointers).
@@ -854,8 +853,93 @@ __device__ void check_direct(const KParams &p, const TileView<P> &tv, int rlo, i
     }
 }
 
+// End of a tile: zero the tile after its last read and, when another tile
+// follows, first save its last two rows (tile rows R-2 and R-1, field P-1 of
+// word rows WR-2 and WR-1, i.e. words 30 and 31 of the 16-byte chunk
+// ((G-1) n_rho + b) * 8 + 7) as the carried rows of the next tile.  The
+// thread that saves a chunk's words is the one that zeroes the chunk, so no
+// barrier separates the two.
+template <int P>
+__device__ void tile_end(const KParams &p, uint32_t *acc, int *carry0, int *carry1, bool save)
+{
+    const int G = p.word_rows >> 5;
+    const int n4 = (p.word_rows * p.n_rho) >> 2;
+    const int c0 = 8 * (G - 1) * p.n_rho;
+    uint4 *acc4 = reinterpret_cast<uint4 *>(acc);
+    for (int i = threadIdx.x; i < n4; i += blockDim.x) {
+        if (save && i >= c0 && (i & 7) == 7) {
+            const uint4 q = acc4[i];
+            const int b = (i - c0) >> 3;
+            carry0[b] = field<P>(q.z, P - 1);
+            carry1[b] = field<P>(q.w, P - 1);
+        }
+        acc4[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+// The 3x3 test of a warp's listed candidates (all lanes call).  The warp's
+// entries are its lanes' column entries, level-major (entry j of every lane
+// holding more than j, in lane order), then its overflow entries.  The column
+// entries are first compacted in place (an entry only moves down, never over
+// an unread one), so that every step gives each lane one entry: within a
+// level the entries come from different lanes, whose word rows -- and so
+// whose tile banks -- differ.  A step runs only while the warp's peak segment
+// has room for 32 more keys; a warp that stops early asks for a merge at the
+// block barrier that ends the round, and continues after it.  Returns when
+// every warp is done (all warps leave through the same barrier).
+template <int P>
+__device__ void check_lists(const KParams &p, const TileView<P> &tv, int ihi, uint32_t *my_cl,
+                            int L, int cnt, int n_ovf, PeakSink &ps, unsigned long long *keys,
+                            unsigned long long *top_stage, WarpCounters wc, const int *vh,
+                            WinScalars &ws)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = lanemask_lt();
+    const int cmax = __reduce_max_sync(0xffffffffu, cnt);
+    int n_cmp = 0;
+    for (int j = 0; j < cmax; ++j) {
+        const bool has = j < cnt;
+        const unsigned m = __ballot_sync(0xffffffffu, has);
+        const uint32_t e = has ? my_cl[j * 32 + lane] : 0u;
+        __syncwarp();
+        if (has)
+            my_cl[n_cmp + __popc(m & lt)] = e;
+        n_cmp += __popc(m);
+    }
+    __syncwarp();
+    const int n_ovf_w = min(n_ovf, p.seg_ovf);
+    const int n_all = n_cmp + n_ovf_w;
+    int y0 = 0;
+    for (;;) {
+        while (y0 < n_all && ps.n <= kSegPk - kSegRoom) {
+            const int y = y0 + lane;
+            bool peak = false;
+            int v = 0, i = 0, b = 0;
+            if (y < n_all) {
+                const uint32_t e = my_cl[y < n_cmp ? y : L * 32 + (y - n_cmp)];
+                decode_entry<P>(p, tv, e, v, i, b);
+                peak = i < ihi && v >= p.T && tv.is_peak(tv.t0 + i, b, v);
+            }
+            record_peaks(peak, v, tv.t0 + i, b, ps);
+            y0 += 32;
+        }
+        if (lane == 0)
+            wc.n_pk[warp] = ps.n;
+        if (!__syncthreads_or(lane == 0 && y0 < n_all))
+            break;
+        merge_peaks(p, keys, top_stage, kSegPk, wc, vh, ws);
+        ps.n = 0;
+        ps.kth = ws.kth;
+        ps.vk = ws.vk;
+    }
+}
+
 // Returns the number of valid hits left in `stage` (in their original order),
-// or -1 when the window was streamed through the stage in parts.
+// or -1 when the window was streamed through the stage in parts.  On entry
+// the tile is all zero (the kernel zeroes it before its first window, and
+// every tile zeroes it again when done); so it is on return.  Per tile the
+// CTA passes three block barriers in the common case: after the votes, at
+// the end of the candidate check, and after the tile is saved and zeroed.
 template <int P, bool F64>
 __device__ int process_tiles(const KParams &p, long long beg, int H, uint32_t *acc, int2 *stage,
                               int *carry, unsigned long long *keys, uint32_t *cl,
@@ -869,10 +953,9 @@ __device__ int process_tiles(const KParams &p, long long beg, int H, uint32_t *a
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int seg_cap = kSegPk;
     int *carry0 = carry, *carry1 = carry + p.n_rho;
-    const int acc_words4 = (WR * p.n_rho) >> 2;
     uint32_t *my_cl = cl + (size_t)warp * p.seg_cl;
-    uint32_t *cmp = cl + (size_t)nw * p.seg_cl;     // the gathered entries
-    (void)lane;
+    const int L = (p.seg_cl - p.seg_ovf) >> 5;      // column slots per lane
+    const ListOvf ovf{wc.n_ovf + warp, p.seg_ovf};
 
     int nv = 0;
     if (single)
@@ -881,15 +964,7 @@ __device__ int process_tiles(const KParams &p, long long beg, int H, uint32_t *a
     for (int tile = 0; tile < n_tiles; ++tile) {
         const int t0 = tile * R;
         const bool last = tile == n_tiles - 1;
-        uint4 *acc4 = reinterpret_cast<uint4 *>(acc);
-        for (int i = threadIdx.x; i < acc_words4; i += blockDim.x)
-            acc4[i] = make_uint4(0u, 0u, 0u, 0u);
-        if (threadIdx.x < 32)
-            wc.n_ovf[threadIdx.x] = 0;
-        __syncthreads();
         int cnt = 0;        // this lane's column entries (a register)
-        const int L = (p.seg_cl - p.seg_ovf) >> 5;
-        const ListOvf ovf{wc.n_ovf + warp, p.seg_ovf};
         const bool fast = !F64 && p.in_range && t0 + R <= p.n_theta;
         TileView<P> tv{acc, carry0, carry1, t0, R, p.lw, p.n_theta, p.n_rho};
         const int rlo = max(t0 - 1, 0);
@@ -911,116 +986,28 @@ __device__ int process_tiles(const KParams &p, long long beg, int H, uint32_t *a
         // the carried row's candidates (it is complete since the previous
         // tile) join the lists before the barrier that ends the vote
         list_carry<P>(p, tv, rlo, rhi, my_cl, L, cnt, ovf);
-        __syncthreads();
-
+        __syncwarp();
+        // barrier: the votes are complete.  An overflow area that overflowed
+        // sends the tile to the direct test of every counter.
+        const bool lost = __syncthreads_or(lane == 0 && *ovf.count > p.seg_ovf);
         if (p.export_acc)
             export_tile<P>(p, acc, t0, R, w);
-        // block-wide exclusive prefix: a warp's entries are its lanes' column
-        // entries in lane order, then its overflow entries (only an overflow
-        // area past its capacity sends the tile to the direct test)
-        int my_pre = 0;             // index of this lane's first column entry
-        int ovf_pre = 0, n_ovf_w = 0;   // index and number of the warp's overflow entries
-        int total = 0;              // entries of the block
-        bool lost;                  // an overflow area overflowed: direct test
-        {
-            const int n_ovf = wc.n_ovf[warp];
-            n_ovf_w = min(n_ovf, p.seg_ovf);
-            const int c = cnt;
-            int incl = c;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, d);
-                if (lane >= d)
-                    incl += y;
-            }
-            if (lane == 31)
-                wc.n_cl[warp] = incl + n_ovf_w;
-            lost = __syncthreads_or(lane == 0 && n_ovf > p.seg_ovf);
-            // every warp scans the warp totals itself (one barrier in all)
-            const int wt = lane < nw ? wc.n_cl[lane] : 0;
-            int wi = wt;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, wi, d);
-                if (lane >= d)
-                    wi += y;
-            }
-            const int pre_w = __shfl_sync(0xffffffffu, wi - wt, warp);
-            total = __shfl_sync(0xffffffffu, wi, 31);
-            my_pre = pre_w + incl - c;
-            ovf_pre = pre_w + __shfl_sync(0xffffffffu, incl, 31);
-        }
         PeakSink ps{keys + p.kp + (size_t)warp * seg_cap, seg_cap, wc.n_pk[warp], 0, ws.kth,
                     ws.vk, vh + warp * kHistBins};
-        if (!lost) {
-            // One thread per listed entry, all warps evenly loaded.  The
-            // entries are first gathered into cmp in a transposed order:
-            // within each block-sized chunk, entry y of the compact order
-            // (owner-major) goes to slot (y % nw) * 32 + y / nw, so that the
-            // lanes of a warp read consecutive slots (no bank conflict) that
-            // hold entries of 32 different owners, whose word rows, and so
-            // whose tile banks, differ.  cmp holds p.cmp_cap entries; larger
-            // lists are taken in rounds.
-            const int B = blockDim.x, lnw = __ffs(nw) - 1;
-            for (int base = 0; base < total; base += p.cmp_cap) {
-                const int hi = min(total - base, p.cmp_cap);
-                auto put = [&](int y, uint32_t e) {
-                    if (y >= 0 && y < hi) {
-                        const int yl = y & (B - 1);
-                        cmp[(y - yl) + ((yl & (nw - 1)) << 5) + (yl >> lnw)] = e;
-                    }
-                };
-                // only this round's entries: [base, base + hi) of the order
-                for (int j = max(0, base - my_pre); j < min(cnt, base + hi - my_pre); ++j)
-                    put(my_pre + j - base, my_cl[j * 32 + lane]);
-                for (int j = max(0, base - ovf_pre) + lane; j < min(n_ovf_w, base + hi - ovf_pre);
-                     j += 32)                                     // the whole warp
-                    put(ovf_pre + j - base, my_cl[L * 32 + j]);
-                __syncthreads();
-                for (int c0 = 0; c0 < hi; c0 += B) {
-                    const int y = c0 + (lane << lnw) + warp;
-                    bool peak = false;
-                    int v = 0, i = 0, b = 0;
-                    if (y < hi) {
-                        decode_entry<P>(p, tv, cmp[c0 + threadIdx.x], v, i, b);
-                        peak = i < ihi && v >= p.T && tv.is_peak(t0 + i, b, v);
-                    }
-                    record_peaks(peak, v, t0 + i, b, ps);
-                    if (lane == 0)
-                        wc.n_pk[warp] = ps.n;
-                    if (__syncthreads_or(lane == 0 && ps.n > seg_cap - kSegRoom)) {
-                        merge_peaks(p, keys, top_stage, seg_cap, wc, vh, ws);
-                        ps.n = 0;
-                        ps.kth = ws.kth;
-                        ps.vk = ws.vk;
-                    }
-                }
-                if (base + p.cmp_cap < total)
-                    __syncthreads();            // the next round rewrites cmp
-            }
-        } else {
+        if (!lost)
+            check_lists<P>(p, tv, ihi, my_cl, L, cnt, *ovf.count, ps, keys, top_stage, wc, vh, ws);
+        else
             check_direct<P>(p, tv, rlo, rhi, ps, keys, top_stage, seg_cap, wc, vh, ws);
-        }
         if (lane == 0) {
             wc.n_pk[warp] = ps.n;
             wc.n_found[warp] += ps.found;
         }
-        // every check step ended in a barrier, so the carried rows are no
-        // longer read: save this tile's last two rows for the next one
-        if (!last) {
-            // rows R-2 and R-1 are two word rows, i.e. two banks: half of a
-            // warp reads each, so every wavefront serves both banks
-            for (int x = threadIdx.x; x < ((p.n_rho + 15) >> 4) << 5; x += blockDim.x) {
-                const int r = (x >> 4) & 1;
-                const int b = ((x >> 5) << 4) | (x & 15);
-                if (b < p.n_rho)
-                    (r ? carry1 : carry0)[b] = tile_val<P>(acc, p.n_rho, p.lw, R - 2 + r, b);
-            }
-        }
-        // keep room for a full step of appends in every segment; this
-        // barrier also ends the tile (the next one clears the accumulator)
-        if (__syncthreads_or(lane == 0 && ps.n > seg_cap - kSegRoom))
-            merge_peaks(p, keys, top_stage, seg_cap, wc, vh, ws);
+        // every check step ended in a barrier, so neither the tile nor the
+        // carried rows are read any more
+        tile_end<P>(p, acc, carry0, carry1, !last);
+        if (threadIdx.x < 32)
+            wc.n_ovf[threadIdx.x] = 0;
+        __syncthreads();
     }
     int pending = 0;
     for (int k = 0; k < nw; ++k)
@@ -1210,6 +1197,12 @@ __global__ void __launch_bounds__(1024, 1) find_kernel(KParams p)
     int *vh = reinterpret_cast<int *>(smem + L.vh);
     int *wtot = reinterpret_cast<int *>(smem + L.wtot);
 
+    // the tile starts all zero; every tile and the association leave it so
+    {
+        uint4 *acc4 = reinterpret_cast<uint4 *>(acc);
+        for (int i = threadIdx.x; i < (p.word_rows * p.n_rho) >> 2; i += blockDim.x)
+            acc4[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
     long long w = blockIdx.x;
     while (w < p.n_windows) {
         long long beg = p.offsets[w], end = p.offsets[w + 1];
@@ -1235,6 +1228,7 @@ __global__ void __launch_bounds__(1024, 1) find_kernel(KParams p)
                 wc.n_pk[threadIdx.x] = 0;
                 wc.n_found[threadIdx.x] = 0;
                 wc.n_cl[threadIdx.x] = 0;
+                wc.n_ovf[threadIdx.x] = 0;
             }
             for (int i = threadIdx.x; i < nw * kHistBins; i += blockDim.x)
                 vh[i] = 0;
@@ -1274,6 +1268,10 @@ __global__ void __launch_bounds__(1024, 1) find_kernel(KParams p)
                 associate<true>(p, w, beg, H, n_top, keys, pk, nv == H ? stage : nullptr, cat_s, wcat, cnt);
             else
                 associate<false>(p, w, beg, H, n_top, keys, pk, nv == H ? stage : nullptr, cat_s, wcat, cnt);
+            // the category counts used the tile: leave it zero for the next window
+            if (wcat == reinterpret_cast<int *>(acc))
+                for (int i = threadIdx.x; i < need; i += blockDim.x)
+                    wcat[i] = 0;
             if (threadIdx.x == 0) {
                 int found = 0;
                 for (int k = 0; k < nw; ++k)
