@@ -940,7 +940,6 @@ int hough_find_host(hough_ctx *ctx, const hough_hits *hits, const int64_t *windo
     size_t total = al(o_acc + acc_per_w * (size_t)n_windows);
     if (total > ctx->stage_bytes) {
         cudaFree(ctx->stage_dev);
-    cudaFree(ctx->d_cf);
         ctx->stage_dev = nullptr;
         ctx->stage_bytes = 0;
         if (cudaMalloc(&ctx->stage_dev, total) != cudaSuccess) {

@@ -57,3 +57,22 @@ def test_lines_and_edge_windows(hough):
     assert (g["fine_theta"][1], g["fine_rho"][1]) == (104, 503)
     assert (g["found"][2:] == 0).all()
     _check(hough, w)
+
+
+def test_tables_survive_host_entry_point_staging(hough):
+    """The two-stage search keeps its tables in the context; the host-buffer
+    find growing its device staging afterwards must leave them in place: the
+    same context gives the same lines before and after."""
+    import torch
+    w = synth.workload("plain", n_windows=200, seed=8)
+    f = hough.Finder(512, 512)
+    a, aht = _gpu(hough, w, f=f)
+    big = synth.generate(3000, ("poisson", 10, 1, 40), (100.0, 300.0), 0.02, seed=9)
+    hh = dict(vane=torch.from_numpy(big.vane).pin_memory(),
+              strip=torch.from_numpy(big.strip).pin_memory())
+    f.find_host(hh, torch.from_numpy(big.offsets))
+    b, bht = _gpu(hough, w, f=f)
+    for name in oracle.CF_DTYPE.names:
+        np.testing.assert_array_equal(a[name], b[name], err_msg=name)
+    np.testing.assert_array_equal(aht, bht)
+    f.close()
