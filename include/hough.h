@@ -545,6 +545,11 @@ typedef struct hough_request_result {
     int64_t arrival_ns;      /* as submitted (or the submit time)                */
     int64_t launch_ns;       /* when its batch was handed to the GPU             */
     int64_t done_ns;         /* when its results were in its host buffers        */
+    /* where its batch's time went (the batch's figures, shared by its
+     * requests): packing into the slot's pinned staging (host clock), copy
+     * in, the find and copy out (CUDA events on the slot's stream), and the
+     * scatter of the results into the requests' buffers (host clock) */
+    int64_t pack_ns, h2d_ns, kernel_ns, d2h_ns, scatter_ns;
 } hough_request_result;
 
 typedef struct hough_server_stats {

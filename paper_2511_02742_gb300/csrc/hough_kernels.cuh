@@ -573,7 +573,8 @@ struct PeakSink {
     int *hist;                 // this warp's row of the vote histogram (null: off)
 };
 
-constexpr int kHistBins = 64;   // per-warp peak-vote histogram; last bin = ">= 63"
+constexpr int kHistBins = 64;
+constexpr int kSerialCompact = 512;    // association: one warp compacts windows up to this size   // per-warp peak-vote histogram; last bin = ">= 63"
 
 __device__ __forceinline__ void record_peaks(bool peak, int v, int t, int b, PeakSink &ps)
 {
@@ -1042,8 +1043,10 @@ __device__ void associate(const KParams &p, long long w, long long beg, int H, i
         pk_s[i] = __ldg(p.S + t);
     }
     const int NC = n_top + 2;
-    for (int q = threadIdx.x; q < nw * NC; q += blockDim.x)
-        wcat[q] = 0;
+    const bool serial = cat_s && H <= kSerialCompact;
+    if (!serial)
+        for (int q = threadIdx.x; q < nw * NC; q += blockDim.x)
+            wcat[q] = 0;
     __syncthreads();
     const int D = p.D, K = p.K;
     const int tol = p.tol;
@@ -1096,6 +1099,69 @@ __device__ void associate(const KParams &p, long long w, long long beg, int H, i
         }
     }
     __syncthreads();
+    if (cat_s && H <= kSerialCompact) {
+        // one warp counts, places and scatters (categories in cat_s): no
+        // per-warp table, three block barriers in all
+        int *ccnt = cat_base, *cbase = cat_base + (HOUGH_MAX_PEAKS + 2);
+        if (warp == 0) {
+            const unsigned lt = lanemask_lt();
+            for (int q = lane; q < NC; q += 32)
+                ccnt[q] = 0;
+            __syncwarp();
+            for (int b0 = 0; b0 < H; b0 += 32) {
+                const int i = b0 + lane;
+                const int cat = i < H ? cat_s[i] : -1;
+                const unsigned m = __match_any_sync(0xffffffffu, cat);
+                if (i < H && lane == __ffs(m) - 1)
+                    ccnt[cat] += __popc(m);
+                __syncwarp();
+            }
+            int run = 0;
+            for (int b0 = 0; b0 < NC; b0 += 32) {
+                const int q = b0 + lane;
+                const int tot = q < NC ? ccnt[q] : 0;
+                int incl = tot;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, d);
+                    if (lane >= d)
+                        incl += y;
+                }
+                const int excl = run + incl - tot;
+                if (q < NC)
+                    cbase[q] = excl;
+                if (q < n_top) {
+                    const unsigned long long k = keys[q];
+                    hough_peak pr;
+                    pr.theta = (uint16_t)((k >> 16) & 0xffffu);
+                    pr.rho = (uint16_t)(k & 0xffffu);
+                    pr.votes = (int32_t)key_votes(k);
+                    pr.n_hits = tot;
+                    pr.hit_begin = excl;
+                    p.peaks[(size_t)w * p.max_peaks + q] = pr;
+                }
+                run += __shfl_sync(0xffffffffu, incl, 31);
+            }
+            __syncwarp();
+            for (int b0 = 0; b0 < H; b0 += 32) {
+                const int i = b0 + lane;
+                const int cat = i < H ? cat_s[i] : -1;
+                const unsigned m = __match_any_sync(0xffffffffu, cat);
+                const int leader = __ffs(m) - 1;
+                int pos = 0;
+                if (i < H && lane == leader) {
+                    pos = cbase[cat];
+                    cbase[cat] = pos + __popc(m);
+                }
+                pos = __shfl_sync(0xffffffffu, pos, leader);
+                if (i < H)
+                    p.track_hits[beg + pos + __popc(m & lt)] = i;
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        return;
+    }
     auto category = [&](int i) {
         if (cat_s)
             return cat_s[i];
@@ -1269,7 +1335,7 @@ __global__ void __launch_bounds__(1024, 1) find_kernel(KParams p)
             else
                 associate<false>(p, w, beg, H, n_top, keys, pk, nv == H ? stage : nullptr, cat_s, wcat, cnt);
             // the category counts used the tile: leave it zero for the next window
-            if (wcat == reinterpret_cast<int *>(acc))
+            if (wcat == reinterpret_cast<int *>(acc) && !(cat_s && H <= kSerialCompact))
                 for (int i = threadIdx.x; i < need; i += blockDim.x)
                     wcat[i] = 0;
             if (threadIdx.x == 0) {

@@ -84,6 +84,8 @@ struct Pending {
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
+    cudaEvent_t t_start = nullptr, t_h2d = nullptr, t_kern = nullptr;   // timing marks
+    int64_t pack_ns = 0, scatter_ns = 0;
     char *d_in = nullptr, *d_out = nullptr;   // device regions
     char *h_in = nullptr, *h_out = nullptr;   // pinned host mirrors
     bool busy = false;
@@ -125,6 +127,7 @@ namespace {
 // server lock (only the worker touches a busy slot).
 int launch_slot(hough_server *s, Slot &sl)
 {
+    const int64_t t_pack = now_ns();
     const InLayout L = in_layout(sl.W, sl.H);
     const OutLayout O = out_layout(sl.W, sl.H, s->max_peaks);
     int64_t *off = reinterpret_cast<int64_t *>(sl.h_in + L.off);
@@ -141,8 +144,11 @@ int launch_slot(hough_server *s, Slot &sl)
         }
     }
     off[sl.W] = sl.H;
-    if (cudaMemcpyAsync(sl.d_in, sl.h_in, L.total, cudaMemcpyHostToDevice, sl.stream) !=
-        cudaSuccess)
+    sl.pack_ns = now_ns() - t_pack;
+    if (cudaEventRecord(sl.t_start, sl.stream) != cudaSuccess ||
+        cudaMemcpyAsync(sl.d_in, sl.h_in, L.total, cudaMemcpyHostToDevice, sl.stream) !=
+            cudaSuccess ||
+        cudaEventRecord(sl.t_h2d, sl.stream) != cudaSuccess)
         return HOUGH_ERR_CUDA;
     hough_hits hits{};
     hits.n_hits = sl.H;
@@ -166,7 +172,8 @@ int launch_slot(hough_server *s, Slot &sl)
                         &t, sl.stream);
     if (rc != HOUGH_OK)
         return rc;
-    if (cudaMemcpyAsync(sl.h_out, sl.d_out, O.total, cudaMemcpyDeviceToHost, sl.stream) !=
+    if (cudaEventRecord(sl.t_kern, sl.stream) != cudaSuccess ||
+        cudaMemcpyAsync(sl.h_out, sl.d_out, O.total, cudaMemcpyDeviceToHost, sl.stream) !=
             cudaSuccess ||
         cudaEventRecord(sl.done, sl.stream) != cudaSuccess)
         return HOUGH_ERR_CUDA;
@@ -212,6 +219,18 @@ void unpack_slot(hough_server *s, Slot &sl)
 void complete_slot(hough_server *s, Slot &sl, int64_t t_done)
 {
     const int nreq = (int)sl.reqs.size();
+    // GPU time of the batch's copy in, find and copy out, from its marks
+    int64_t gpu_ns[3] = {0, 0, 0};
+    if (sl.status == HOUGH_OK) {
+        const cudaEvent_t ev[4] = {sl.t_start, sl.t_h2d, sl.t_kern, sl.done};
+        for (int k = 0; k < 3; ++k) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev[k], ev[k + 1]) == cudaSuccess)
+                gpu_ns[k] = (int64_t)(ms * 1e6);
+            else
+                cudaGetLastError();
+        }
+    }
     for (const Pending &p : sl.reqs) {
         hough_request_result r{};
         r.ticket = p.ticket;
@@ -221,6 +240,11 @@ void complete_slot(hough_server *s, Slot &sl, int64_t t_done)
         r.arrival_ns = p.req.arrival_ns;
         r.launch_ns = sl.launch_ns;
         r.done_ns = t_done;
+        r.pack_ns = sl.pack_ns;
+        r.h2d_ns = gpu_ns[0];
+        r.kernel_ns = gpu_ns[1];
+        r.d2h_ns = gpu_ns[2];
+        r.scatter_ns = sl.scatter_ns;
         s->done[p.ticket] = r;
         s->done_order.push_back(p.ticket);
     }
@@ -251,9 +275,11 @@ void worker_loop(hough_server *s)
                 sl.status = HOUGH_ERR_CUDA;
             }
             lk.unlock();
+            const int64_t t_sc = now_ns();
             if (sl.status == HOUGH_OK)
                 unpack_slot(s, sl);
             const int64_t t = now_ns();
+            sl.scatter_ns = t - t_sc;
             lk.lock();
             complete_slot(s, sl, t);
             progress = true;
@@ -326,8 +352,9 @@ void free_slots(hough_server *s)
         cudaFree(sl.d_out);
         cudaFreeHost(sl.h_in);
         cudaFreeHost(sl.h_out);
-        if (sl.done)
-            cudaEventDestroy(sl.done);
+        for (cudaEvent_t e : {sl.done, sl.t_start, sl.t_h2d, sl.t_kern})
+            if (e)
+                cudaEventDestroy(e);
         if (sl.stream)
             cudaStreamDestroy(sl.stream);
     }
@@ -382,7 +409,8 @@ int hough_server_create(hough_ctx *ctx, const hough_server_config *cfg, hough_se
     int rc = HOUGH_OK;
     for (Slot &sl : s->slots) {
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaEventCreate(&sl.done) != cudaSuccess || cudaEventCreate(&sl.t_start) != cudaSuccess ||
+            cudaEventCreate(&sl.t_h2d) != cudaSuccess || cudaEventCreate(&sl.t_kern) != cudaSuccess) {
             rc = HOUGH_ERR_CUDA;
             break;
         }

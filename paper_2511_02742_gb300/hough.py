@@ -89,7 +89,9 @@ class hough_request_result(ctypes.Structure):
     _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32),
                 ("batch_requests", ctypes.c_int32), ("batch_windows", ctypes.c_int64),
                 ("arrival_ns", ctypes.c_int64), ("launch_ns", ctypes.c_int64),
-                ("done_ns", ctypes.c_int64)]
+                ("done_ns", ctypes.c_int64), ("pack_ns", ctypes.c_int64),
+                ("h2d_ns", ctypes.c_int64), ("kernel_ns", ctypes.c_int64),
+                ("d2h_ns", ctypes.c_int64), ("scatter_ns", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

@@ -360,3 +360,24 @@ def test_hit_arrays_at_any_alignment(hough, shift_a, shift_b):
         torch.cuda.synchronize()
         assert_batch_equal(to_numpy(out, w.n_hits), ref, w)
     f.close()
+
+
+def test_windows_past_255_hits_try_8bit_counters_first(hough):
+    """Windows of 256 to 65535 hits run on 8-bit counters first and are redone
+    with 16-bit counters when one would wrap: 300 hits at one (phi, z) put 300
+    votes in one bin of every row (redone); 260 stacked hits plus 100 random
+    ones, and 400 random hits, stay within 8 bits.  Both forms equal the
+    oracle, accumulators included."""
+    rng = np.random.default_rng(9)
+    parts = [([7] * 300, [1500] * 300),
+             (rng.integers(0, 40, 400), rng.integers(0, 2048, 400)),
+             ([3] * 255, [100] * 255),
+             (np.r_[[9] * 255, rng.integers(0, 40, 100)], np.r_[[700] * 255, rng.integers(0, 2048, 100)]),
+             (np.r_[[9] * 256, rng.integers(0, 40, 100)], np.r_[[700] * 256, rng.integers(0, 2048, 100)])]
+    w = _windows_from_arrays(parts)
+    for export in (False, True):
+        ref = oracle_run(w, 128, 512, export=export)
+        assert ref["peaks"][0][0]["votes"] == 300
+        f = _finder(hough, 128, 512, export_acc=export)
+        assert_batch_equal(gpu_run(f, w), ref, w, check_acc=export)
+        f.close()
