@@ -362,12 +362,11 @@ def test_hit_arrays_at_any_alignment(hough, shift_a, shift_b):
     f.close()
 
 
-def test_windows_past_255_hits_try_8bit_counters_first(hough):
-    """Windows of 256 to 65535 hits run on 8-bit counters first and are redone
-    with 16-bit counters when one would wrap: 300 hits at one (phi, z) put 300
-    votes in one bin of every row (redone); 260 stacked hits plus 100 random
-    ones, and 400 random hits, stay within 8 bits.  Both forms equal the
-    oracle, accumulators included."""
+def test_windows_around_the_8bit_counter_limit(hough):
+    """Windows on both sides of the 255-hit limit of 8-bit counters: 255
+    stacked hits (8-bit, a bin of 255), 300 and 256+100 hits (16-bit, bins
+    of 300 and 256), 400 random hits.  Equal to the oracle, accumulators
+    included."""
     rng = np.random.default_rng(9)
     parts = [([7] * 300, [1500] * 300),
              (rng.integers(0, 40, 400), rng.integers(0, 2048, 400)),
