@@ -471,46 +471,73 @@ def _busy_overlap(results):
     return (area / t_any if t_any else 0.0), (t_two / t_any if t_any else 0.0), peak
 
 
-def _serve_point(srv, pool, ref, out, vane, strip, rate, seconds, slice_ms, seed):
+def _serve_point(srv, pool, ref, out, vane, strip, rate, seconds, slice_ms, seed, check_every):
     """One load point: windows arrive as a Poisson process at `rate`
     windows/s; every slice_ms the windows that arrived form one time slice,
     submitted when the slice ends.  Latency = results in the request's host
     buffers minus the slice's end.  Windows are drawn cyclically from the
-    pool; every completed slice is compared with the pool's one-launch
-    results (the same windows alone)."""
+    pool.  check_every = 1: every completed slice is compared with the pool's
+    one-launch results (the same windows alone) as it completes.  Otherwise,
+    so that checking cannot slow the submitting loop, every check_every-th
+    slice writes to buffers of its own and is compared after the run, and the
+    other slices' results (in the pool's buffers) are compared after the run
+    too."""
+    import torch
     from paper_2511_02742_gb300 import hough
     clock = hough.hough_server_clock_ns
     win_keys = ("peaks", "n_peaks", "n_found", "window_status")
     dt_ns = int(slice_ms * 1e6)
     n_slices = max(1, int(round(seconds * 1e3 / slice_ms)))
     counts = np.random.default_rng(seed).poisson(rate * dt_ns * 1e-9, n_slices)
+    peak_slot = np.arange(ref["peaks"].shape[1])
+
+    def same(o, a, b):
+        h0, h1 = int(pool.offsets[a]), int(pool.offsets[b])
+        kept = peak_slot[None, :] < ref["n_peaks"][a:b, None]
+        return (np.array_equal(o["n_peaks"], ref["n_peaks"][a:b]) and
+                np.array_equal(o["window_status"], ref["window_status"][a:b]) and
+                np.array_equal(o["hit_track"], ref["hit_track"][h0:h1]) and
+                np.array_equal(o["track_hits"], ref["track_hits"][h0:h1]) and
+                np.array_equal(o["peaks"][kept], ref["peaks"][a:b][kept]))
+
+    # the slices, laid out before the timed loop
+    plan, pos = [], 0
+    for i, c in enumerate(counts):
+        if c == 0:
+            continue
+        if pos + c > pool.n_windows:
+            pos = 0
+        a, b = pos, pos + int(c)
+        pos = b
+        h0, h1 = int(pool.offsets[a]), int(pool.offsets[b])
+        if check_every > 1 and len(plan) % check_every == 0:
+            o = {k: np.zeros_like(out[k][a:b] if k in win_keys else out[k][h0:h1])
+                 for k in out}
+            o = {k: torch.from_numpy(v).pin_memory().numpy() for k, v in o.items()}
+            private = True
+        else:
+            o = {k: (out[k][a:b] if k in win_keys else out[k][h0:h1]) for k in out}
+            private = False
+        plan.append((i, a, b, h0, h1, pool.offsets[a:b + 1] - h0, o, private))
     ranges, res = {}, []
     state = {"mism": 0, "done": 0, "last_done": 0}
-    peak_slot = np.arange(ref["peaks"].shape[1])
 
     def handle(rs):
         for r in rs:
-            a, b = ranges.pop(r["ticket"])
+            a, b, o, private = ranges.pop(r["ticket"])
             res.append(r)
             state["last_done"] = max(state["last_done"], r["done_ns"])
             state["done"] += b - a
-            h0, h1 = int(pool.offsets[a]), int(pool.offsets[b])
-            # a few vectorised comparisons per slice, so that checking stays
-            # well inside the time between arrivals
-            kept = peak_slot[None, :] < ref["n_peaks"][a:b, None]
-            ok = r["status"] == 0 and \
-                np.array_equal(out["n_peaks"][a:b], ref["n_peaks"][a:b]) and \
-                np.array_equal(out["window_status"][a:b], ref["window_status"][a:b]) and \
-                np.array_equal(out["hit_track"][h0:h1], ref["hit_track"][h0:h1]) and \
-                np.array_equal(out["track_hits"][h0:h1], ref["track_hits"][h0:h1]) and \
-                np.array_equal(out["peaks"][a:b][kept], ref["peaks"][a:b][kept])
-            state["mism"] += 0 if ok else 1
+            if r["status"] != 0:
+                state["mism"] += 1
+            elif check_every == 1:
+                state["mism"] += 0 if same(o, a, b) else 1
 
     gc.collect()
     gc.disable()            # no collector pauses inside the timed arrival loop
     t0 = clock() + 5_000_000
-    pos, submitted, late, busy_refused = 0, 0, 0, 0
-    for i, c in enumerate(counts):
+    submitted, late, busy_refused = 0, 0, 0
+    for i, a, b, h0, h1, offs, o, private in plan:
         t_arr = t0 + (i + 1) * dt_ns
         while True:
             now = clock()
@@ -519,29 +546,31 @@ def _serve_point(srv, pool, ref, out, vane, strip, rate, seconds, slice_ms, seed
             handle(srv.poll(1024))
             if t_arr - clock() > 300_000:
                 time.sleep(1e-4)
-        if c == 0:
-            continue
-        if pos + c > pool.n_windows:
-            pos = 0
-        a, b = pos, pos + int(c)
-        pos = b
-        h0, h1 = int(pool.offsets[a]), int(pool.offsets[b])
-        o = {k: (out[k][a:b] if k in win_keys else out[k][h0:h1]) for k in out}
         late += 1 if clock() - t_arr > 100_000 else 0
         while True:
             try:
-                tk = srv.submit(vane[h0:h1], strip[h0:h1], pool.offsets[a:b + 1] - h0, o, t_arr)
+                tk = srv.submit(vane[h0:h1], strip[h0:h1], offs, o, t_arr)
                 break
             except hough.HoughError as e:       # queue full: take results, retry
                 if e.code != hough.HOUGH_ERR_BUSY:
                     raise
                 busy_refused += 1
                 handle(srv.poll(1024))
-        ranges[tk] = (a, b)
+        ranges[tk] = (a, b, o, private)
         submitted += b - a
     srv.drain(600_000)
     handle(srv.poll(1 << 16))
     gc.enable()
+    checked = len(res) if check_every == 1 else 0
+    if check_every > 1:
+        for _, a, b, _, _, _, o, private in plan:
+            if private:
+                checked += 1
+                state["mism"] += 0 if same(o, a, b) else 1
+        served = sorted({(p[1], p[2]) for p in plan if not p[7]})
+        state["mism"] += sum(0 if same({k: (out[k][a:b] if k in win_keys else
+                                            out[k][int(pool.offsets[a]):int(pool.offsets[b])])
+                                        for k in out}, a, b) else 1 for a, b in served)
     span_s = (state["last_done"] - t0) * 1e-9
 
     def pct(key, q):
@@ -554,7 +583,7 @@ def _serve_point(srv, pool, ref, out, vane, strip, rate, seconds, slice_ms, seed
     mean_busy, share_two, peak_busy = _busy_overlap(res)
     return {"offered_windows_per_s": round(submitted / (n_slices * dt_ns * 1e-9), 1),
             "windows_per_s": round(state["done"] / span_s, 1) if span_s > 0 else None,
-            "slice_ms": slice_ms, "requests": len(res), "windows": state["done"],
+            "slice_ms": round(slice_ms, 4), "requests": len(res), "windows": state["done"],
             "p50_us": round(float(np.percentile(lat, 50)), 1),
             "p99_us": round(float(np.percentile(lat, 99)), 1),
             "max_us": round(float(lat.max()), 1),
@@ -569,7 +598,7 @@ def _serve_point(srv, pool, ref, out, vane, strip, rate, seconds, slice_ms, seed
                                  "launch_to_done": round(float(np.percentile(l2d, 50)), 1),
                                  "unaccounted": round(float(np.percentile(l2d - parts, 50)), 1)},
             "late_submits": late, "busy_refusals": busy_refused,
-            "mismatched_slices": state["mism"]}
+            "checked_slices": checked, "mismatched_slices": state["mism"]}
 
 
 def _serving_leg(args, dev):
@@ -593,18 +622,18 @@ def _serving_leg(args, dev):
            f.alloc_outputs(pool.n_windows, pool.n_hits, device="cpu", pin=True).items()}
     launch = [int(x) for x in args.serve_launch.split(",")] if args.serve_launch else None
     launch_used = (dict(zip(("threads", "word_rows", "hit_stage", "ctas_per_sm"), launch))
-                   if launch else "server default: 512 threads, 1 CTA per SM, largest tile, "
+                   if launch else "server default: 1024 threads, 1 CTA per SM, largest tile, "
                                   "2048-hit stage")
     srv = hough.Server(f, n_slots=4, slot_windows=4096, slot_hits=1 << 21, max_queued=1 << 16,
                        launch=launch)
     base = _serve_point(srv, pool, ref, out, vane, strip, args.serve_rate, args.serve_seconds,
-                        args.serve_slice_ms, 11)
+                        args.serve_slice_ms, 11, 1)
     sweep = []
     for k, rate in enumerate(float(x) for x in args.serve_sweep.split(",") if x):
         # slices of at most ~1000 windows, so that several fit in one slot
         sm = min(args.serve_slice_ms, 1000.0 / (rate * 1e-3))
         sweep.append(dict({"rate": rate}, **_serve_point(srv, pool, ref, out, vane, strip, rate,
-                                                         args.serve_sweep_seconds, sm, 12 + k)))
+                                                         args.serve_sweep_seconds, sm, 12 + k, 16)))
     st = srv.stats()
     srv.close()
     f.close()

@@ -488,9 +488,10 @@ int hough_find_noalloc(const hough_geometry *g, int n_theta, int n_rho,
  *   - admits queued requests, oldest first, into a free batch slot while the
  *     slot's device memory has room for their windows and hits (admission by
  *     memory: a slot holds at most slot_windows windows and slot_hits hits);
- *   - runs each slot as one copy in, one launch of the find kernel and one
- *     copy out, on the slot's own stream;
- *   - copies each request's results into its host buffers and completes it.
+ *   - runs each slot on its own stream: the batch's window offsets (rebased
+ *     to the batch) and each request's hits are copied in, the find kernel
+ *     runs once over the batch, and each request's results are copied
+ *     straight into its host buffers; the request then completes.
  * With n_slots > 1, requests that arrive while earlier batches are on the
  * GPU go into the next free slot at once (continuous batching), so their
  * copies and kernels overlap with the running ones.  Device buffers and
@@ -502,7 +503,9 @@ int hough_find_noalloc(const hough_geometry *g, int n_theta, int n_rho,
  * context (hough_find, hough_set_launch, ...) until hough_server_destroy.
  * Server calls may be made from any host thread.  While batches are on the
  * GPU the worker polls their completion events (yielding between polls), so
- * it keeps one host core busy; it sleeps when nothing is queued or running.
+ * it keeps one host core busy; when nothing is queued or running it polls the
+ * queue for 2 ms more (a sleeping thread takes tens of microseconds to wake)
+ * and then sleeps.
  */
 typedef struct hough_server hough_server;
 
@@ -512,9 +515,10 @@ typedef struct hough_server_config {
     int64_t slot_windows;  /* windows one batch can hold (>= 1)                         */
     int64_t slot_hits;     /* hits one batch can hold (>= 1)                            */
     int64_t max_queued;    /* requests waiting for a slot before submit says BUSY (>= 1) */
-    hough_launch launch;   /* launch shape of the server's batches; all 0: one CTA per
-                              SM with the largest tile (the lowest latency for small
-                              batches), restored on the context by hough_server_destroy */
+    hough_launch launch;   /* launch shape of the server's batches; all 0: one CTA of
+                              1024 threads per SM with the largest tile (the lowest
+                              latency for small batches); the context's own shape is
+                              restored by hough_server_destroy */
 } hough_server_config;
 
 /*
@@ -523,8 +527,13 @@ typedef struct hough_server_config {
  * host array of n_windows + 1 int64 starting at 0 and non-decreasing.  out
  * holds HOST buffers laid out as for hough_find (peaks[n_windows*max_peaks],
  * n_peaks, n_found (may be NULL), hit_track[n_hits], track_hits[n_hits],
- * window_status; acc is not supported).  Every buffer must stay valid and
- * untouched until the request completes.  arrival_ns: when the slice arrived,
+ * window_status; acc is not supported).  The copies go straight between these
+ * buffers and the device, so they should be page-locked (cudaHostAlloc or
+ * cudaHostRegister): pageable buffers work, but the driver then stages each
+ * copy and the worker waits on it.  Unlike hough_find, the whole
+ * peaks[n_windows*max_peaks] array is written (entries past n_peaks[w] hold
+ * unspecified values).  Every buffer must stay valid and untouched until the
+ * request completes.  arrival_ns: when the slice arrived,
  * on the hough_server_clock_ns clock (0 = at submit); latencies are measured
  * from it.
  */

@@ -3,15 +3,16 @@
 //
 // A server owns n_slots batch slots.  Each slot has its own stream, a device
 // input region (offsets | in0 | in1), a device output region (peaks | n_peaks
-// | n_found | status | hit_track | track_hits) and pinned host mirrors of
-// both, all allocated once.  One worker thread loops over:
-//   retire  -- a busy slot whose completion event has fired: scatter its
-//              output mirror into the requests' host buffers, complete them;
+// | n_found | status | hit_track | track_hits) and a pinned staging area for
+// the batch's window offsets, all allocated once.  One worker thread loops over:
+//   retire  -- a busy slot whose completion event has fired: complete its
+//              requests (their results are in their buffers already);
 //   admit   -- a free slot and a non-empty queue: take requests, oldest
-//              first, while the slot's window and hit capacity allows, pack
-//              them into the input mirror (offsets rebased to the batch),
-//              then copy in, launch the find kernel and copy out on the
-//              slot's stream, and record its event.
+//              first, while the slot's window and hit capacity allows,
+//              write the batch's window offsets (rebased) into the slot's
+//              pinned staging, then on the slot's stream copy them and each
+//              request's hits in, launch the find kernel, copy the results
+//              straight into each request's buffers, and record its event.
 // Windows never interact (each is its own unit of work), so packing
 // requests together changes no result: a window's outputs depend only on its
 // own hits, and all per-window outputs are window-local (peak indices,
@@ -19,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -36,6 +38,9 @@
 namespace {
 
 size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// How long an idle worker polls the queue before it sleeps.
+constexpr int64_t kIdleSpinNs = 2'000'000;
 
 int64_t now_ns()
 {
@@ -87,7 +92,7 @@ struct Slot {
     cudaEvent_t t_start = nullptr, t_h2d = nullptr, t_kern = nullptr;   // timing marks
     int64_t pack_ns = 0, scatter_ns = 0;
     char *d_in = nullptr, *d_out = nullptr;   // device regions
-    char *h_in = nullptr, *h_out = nullptr;   // pinned host mirrors
+    char *h_in = nullptr;                     // pinned staging of the batch's offsets
     bool busy = false;
     std::vector<Pending> reqs;
     std::vector<int64_t> win_base, hit_base;
@@ -103,7 +108,7 @@ struct hough_server {
     hough_server_config cfg{};
     hough_launch saved_launch{};     // the context's shape before the server
     int max_peaks = 0;
-    size_t in_cap = 0, out_cap = 0;
+    size_t in_cap = 0, out_cap = 0, stage_cap = 0;
     std::vector<Slot> slots;
 
     std::mutex mu;
@@ -117,6 +122,8 @@ struct hough_server {
     int64_t in_flight = 0;
     hough_server_stats st{};
     bool stop = false;
+    std::atomic<int64_t> queued{0};       // queue length, read without the lock
+    std::atomic<bool> stopping{false};
     std::thread worker;
 };
 
@@ -130,25 +137,34 @@ int launch_slot(hough_server *s, Slot &sl)
     const int64_t t_pack = now_ns();
     const InLayout L = in_layout(sl.W, sl.H);
     const OutLayout O = out_layout(sl.W, sl.H, s->max_peaks);
+    const int mp = s->max_peaks;
     int64_t *off = reinterpret_cast<int64_t *>(sl.h_in + L.off);
-    int32_t *a = reinterpret_cast<int32_t *>(sl.h_in + L.in0);
-    int32_t *b = reinterpret_cast<int32_t *>(sl.h_in + L.in1);
     for (size_t k = 0; k < sl.reqs.size(); ++k) {
         const hough_request &r = sl.reqs[k].req;
-        const int64_t wb = sl.win_base[k], hb = sl.hit_base[k], nh = sl.reqs[k].n_hits;
+        const int64_t wb = sl.win_base[k], hb = sl.hit_base[k];
         for (int64_t j = 0; j < r.n_windows; ++j)
             off[wb + j] = hb + r.window_offsets[j];
-        if (nh > 0) {
-            std::memcpy(a + hb, r.in0, 4 * (size_t)nh);
-            std::memcpy(b + hb, r.in1, 4 * (size_t)nh);
-        }
     }
     off[sl.W] = sl.H;
     sl.pack_ns = now_ns() - t_pack;
-    if (cudaEventRecord(sl.t_start, sl.stream) != cudaSuccess ||
-        cudaMemcpyAsync(sl.d_in, sl.h_in, L.total, cudaMemcpyHostToDevice, sl.stream) !=
-            cudaSuccess ||
-        cudaEventRecord(sl.t_h2d, sl.stream) != cudaSuccess)
+    auto in = [&](void *dst, const void *src, size_t n) {
+        return n == 0 || cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, sl.stream) ==
+                             cudaSuccess;
+    };
+    auto out = [&](void *dst, const void *src, size_t n) {
+        return n == 0 || cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, sl.stream) ==
+                             cudaSuccess;
+    };
+    // copy in: the rebased offsets from the staging, each request's hits
+    // straight from its own buffers
+    bool ok = cudaEventRecord(sl.t_start, sl.stream) == cudaSuccess &&
+              in(sl.d_in + L.off, sl.h_in + L.off, 8 * (size_t)(sl.W + 1));
+    for (size_t k = 0; ok && k < sl.reqs.size(); ++k) {
+        const hough_request &r = sl.reqs[k].req;
+        const size_t hb = (size_t)sl.hit_base[k], nh = (size_t)sl.reqs[k].n_hits;
+        ok = in(sl.d_in + L.in0 + 4 * hb, r.in0, 4 * nh) && in(sl.d_in + L.in1 + 4 * hb, r.in1, 4 * nh);
+    }
+    if (!ok || cudaEventRecord(sl.t_h2d, sl.stream) != cudaSuccess)
         return HOUGH_ERR_CUDA;
     hough_hits hits{};
     hits.n_hits = sl.H;
@@ -172,47 +188,23 @@ int launch_slot(hough_server *s, Slot &sl)
                         &t, sl.stream);
     if (rc != HOUGH_OK)
         return rc;
-    if (cudaEventRecord(sl.t_kern, sl.stream) != cudaSuccess ||
-        cudaMemcpyAsync(sl.h_out, sl.d_out, O.total, cudaMemcpyDeviceToHost, sl.stream) !=
-            cudaSuccess ||
-        cudaEventRecord(sl.done, sl.stream) != cudaSuccess)
+    // copy out, straight into each request's buffers
+    ok = cudaEventRecord(sl.t_kern, sl.stream) == cudaSuccess;
+    for (size_t k = 0; ok && k < sl.reqs.size(); ++k) {
+        const hough_request &r = sl.reqs[k].req;
+        const size_t wb = (size_t)sl.win_base[k], hb = (size_t)sl.hit_base[k];
+        const size_t nw = (size_t)r.n_windows, nh = (size_t)sl.reqs[k].n_hits;
+        ok = out(r.out.n_peaks, sl.d_out + O.np + 4 * wb, 4 * nw) &&
+             out(r.out.window_status, sl.d_out + O.st + 4 * wb, 4 * nw) &&
+             (!r.out.n_found || out(r.out.n_found, sl.d_out + O.nf + 4 * wb, 4 * nw)) &&
+             (mp == 0 || out(r.out.peaks, sl.d_out + O.pk + sizeof(hough_peak) * wb * mp,
+                             sizeof(hough_peak) * nw * mp)) &&
+             out(r.out.hit_track, sl.d_out + O.ht + 4 * hb, 4 * nh) &&
+             out(r.out.track_hits, sl.d_out + O.th + 4 * hb, 4 * nh);
+    }
+    if (!ok || cudaEventRecord(sl.done, sl.stream) != cudaSuccess)
         return HOUGH_ERR_CUDA;
     return HOUGH_OK;
-}
-
-// Scatter a finished slot's output mirror into its requests' host buffers.
-void unpack_slot(hough_server *s, Slot &sl)
-{
-    const int mp = s->max_peaks;
-    const OutLayout O = out_layout(sl.W, sl.H, mp);
-    const hough_peak *pk = reinterpret_cast<const hough_peak *>(sl.h_out + O.pk);
-    const int32_t *np = reinterpret_cast<const int32_t *>(sl.h_out + O.np);
-    const int32_t *nf = reinterpret_cast<const int32_t *>(sl.h_out + O.nf);
-    const uint32_t *st = reinterpret_cast<const uint32_t *>(sl.h_out + O.st);
-    const int32_t *ht = reinterpret_cast<const int32_t *>(sl.h_out + O.ht);
-    const int32_t *th = reinterpret_cast<const int32_t *>(sl.h_out + O.th);
-    for (size_t k = 0; k < sl.reqs.size(); ++k) {
-        const hough_request &r = sl.reqs[k].req;
-        const int64_t wb = sl.win_base[k], hb = sl.hit_base[k], nw = r.n_windows,
-                      nh = sl.reqs[k].n_hits;
-        if (nw > 0) {
-            std::memcpy(r.out.n_peaks, np + wb, 4 * (size_t)nw);
-            std::memcpy(r.out.window_status, st + wb, 4 * (size_t)nw);
-            if (r.out.n_found)
-                std::memcpy(r.out.n_found, nf + wb, 4 * (size_t)nw);
-            if (mp > 0)
-                for (int64_t j = 0; j < nw; ++j) {
-                    const int n = std::min(std::max(np[wb + j], 0), mp);
-                    if (n > 0)
-                        std::memcpy(r.out.peaks + j * mp, pk + (wb + j) * mp,
-                                    sizeof(hough_peak) * (size_t)n);
-                }
-        }
-        if (nh > 0) {
-            std::memcpy(r.out.hit_track, ht + hb, 4 * (size_t)nh);
-            std::memcpy(r.out.track_hits, th + hb, 4 * (size_t)nh);
-        }
-    }
 }
 
 // Complete every request of a slot (lock held) and free the slot.
@@ -274,14 +266,8 @@ void worker_loop(hough_server *s)
                 cudaGetLastError();
                 sl.status = HOUGH_ERR_CUDA;
             }
-            lk.unlock();
-            const int64_t t_sc = now_ns();
-            if (sl.status == HOUGH_OK)
-                unpack_slot(s, sl);
-            const int64_t t = now_ns();
-            sl.scatter_ns = t - t_sc;
-            lk.lock();
-            complete_slot(s, sl, t);
+            sl.scatter_ns = 0;
+            complete_slot(s, sl, now_ns());
             progress = true;
         }
         // admit
@@ -304,6 +290,7 @@ void worker_loop(hough_server *s)
                 sl.H += p.n_hits;
                 sl.reqs.push_back(p);
                 s->queue.pop_front();
+                s->queued.fetch_sub(1, std::memory_order_release);
             }
             sl.busy = true;
             s->in_flight += (int64_t)sl.reqs.size();
@@ -338,6 +325,14 @@ void worker_loop(hough_server *s)
             std::this_thread::yield();
             lk.lock();
         } else {
+            // idle: poll the queue for a while before sleeping, since a
+            // sleeping worker takes tens of microseconds to wake
+            lk.unlock();
+            const int64_t until = now_ns() + kIdleSpinNs;
+            while (s->queued.load(std::memory_order_acquire) == 0 && !s->stopping.load() &&
+                   now_ns() < until)
+                std::this_thread::yield();
+            lk.lock();
             s->cv_work.wait(lk, [s] { return s->stop || !s->queue.empty(); });
         }
     }
@@ -351,7 +346,6 @@ void free_slots(hough_server *s)
         cudaFree(sl.d_in);
         cudaFree(sl.d_out);
         cudaFreeHost(sl.h_in);
-        cudaFreeHost(sl.h_out);
         for (cudaEvent_t e : {sl.done, sl.t_start, sl.t_h2d, sl.t_kern})
             if (e)
                 cudaEventDestroy(e);
@@ -391,12 +385,13 @@ int hough_server_create(hough_ctx *ctx, const hough_server_config *cfg, hough_se
     s->ctx = ctx;
     s->cfg = *cfg;
     s->max_peaks = ctx->th.max_peaks;
-    // the server's launch shape: as given, else one CTA per SM with the
-    // largest tile (small batches then spread over every SM)
+    // the server's launch shape: as given, else one CTA of 1024 threads per
+    // SM with the largest tile (small batches then spread over every SM, and
+    // each window has the most warps)
     s->saved_launch = ctx->launch;
     hough_launch want = cfg->launch;
     if (want.threads == 0 && want.word_rows == 0 && want.hit_stage == 0 && want.ctas_per_sm == 0)
-        want = hough_launch{512, 0, 2048, 1};
+        want = hough_launch{1024, 0, 2048, 1};
     if (hough_set_launch(ctx, &want) != HOUGH_OK) {
         ctx->launch = s->saved_launch;
         delete s;
@@ -404,6 +399,7 @@ int hough_server_create(hough_ctx *ctx, const hough_server_config *cfg, hough_se
         return HOUGH_ERR_INVALID_ARG;
     }
     s->in_cap = in_layout(cfg->slot_windows, cfg->slot_hits).total;
+    s->stage_cap = 8 * (size_t)(cfg->slot_windows + 1);
     s->out_cap = out_layout(cfg->slot_windows, cfg->slot_hits, s->max_peaks).total;
     s->slots.resize(cfg->n_slots);
     int rc = HOUGH_OK;
@@ -416,13 +412,12 @@ int hough_server_create(hough_ctx *ctx, const hough_server_config *cfg, hough_se
         }
         if (cudaMalloc(&sl.d_in, s->in_cap) != cudaSuccess ||
             cudaMalloc(&sl.d_out, s->out_cap) != cudaSuccess ||
-            cudaHostAlloc(&sl.h_in, s->in_cap, cudaHostAllocDefault) != cudaSuccess ||
-            cudaHostAlloc(&sl.h_out, s->out_cap, cudaHostAllocDefault) != cudaSuccess) {
+            cudaHostAlloc(&sl.h_in, s->stage_cap, cudaHostAllocDefault) != cudaSuccess) {
             rc = HOUGH_ERR_ALLOC;
             break;
         }
         s->st.device_bytes += (int64_t)(s->in_cap + s->out_cap);
-        s->st.host_bytes += (int64_t)(s->in_cap + s->out_cap);
+        s->st.host_bytes += (int64_t)s->stage_cap;
     }
     // one empty window per slot stream: the context sets up its per-stream
     // scheduling counters now, not in the middle of serving
@@ -491,6 +486,7 @@ int hough_server_submit(hough_server *s, const hough_request *req, uint64_t *tic
     if (p.req.arrival_ns == 0)
         p.req.arrival_ns = now_ns();
     s->queue.push_back(p);
+    s->queued.fetch_add(1, std::memory_order_release);
     s->live.insert(p.ticket);
     s->st.submitted += 1;
     *ticket = p.ticket;
@@ -569,6 +565,7 @@ void hough_server_destroy(hough_server *s)
     {
         std::lock_guard<std::mutex> lk(s->mu);
         s->stop = true;
+        s->stopping.store(true);
     }
     s->cv_work.notify_all();
     if (s->worker.joinable())

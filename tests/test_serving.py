@@ -198,3 +198,32 @@ def test_request_buffers_are_checked_before_submission():
         assert srv.wait(t, 60000)["status"] == 0
     finally:
         srv.close()
+
+
+def test_pageable_request_buffers():
+    """Requests whose hits and result buffers are ordinary (pageable) host
+    memory: the copies are staged by the driver, the results are the same."""
+    from paper_2511_02742_gb300 import hough
+    cfg = synth.WORKLOADS["serving"]
+    w = synth.workload("serving", n_windows=120, seed=8)
+    f = hough.Finder(cfg["n_theta"], cfg["n_rho"])
+    ref = _reference(hough, f, w)
+    srv = hough.Server(f, n_slots=2, slot_windows=256, slot_hits=1 << 18)
+    vane, strip = w.vane.copy(), w.strip.copy()
+    tickets = []
+    for a, b in _slices(w, [40, 1, 79]):
+        h0, h1 = int(w.offsets[a]), int(w.offsets[b])
+        n = b - a
+        out = {"peaks": np.zeros((n, f.max_peaks, 4), np.int32),
+               "n_peaks": np.zeros(n, np.int32), "n_found": np.zeros(n, np.int32),
+               "hit_track": np.zeros(max(h1 - h0, 1), np.int32),
+               "track_hits": np.zeros(max(h1 - h0, 1), np.int32),
+               "window_status": np.zeros(n, np.int32)}
+        t = srv.submit(vane[h0:h1], strip[h0:h1], (w.offsets[a:b + 1] - h0).astype(np.int64), out)
+        tickets.append((t, a, b, out))
+    for t, a, b, out in tickets:
+        assert srv.wait(t, 10000)["status"] == 0
+        import torch
+        _check(ref, w, a, b, {k: torch.from_numpy(v) for k, v in out.items()}, f.max_peaks)
+    srv.close()
+    f.close()
