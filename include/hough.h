@@ -465,9 +465,13 @@ int hough_autotune(hough_ctx *ctx, const hough_hits *hits, const int64_t *window
  *     array's device address (set-up); make that first call before any stream
  *     capture.
  *   - Every call on a device shares the array and leaves its contents behind:
- *     the call clears the counters and rewrites the tables on its stream
- *     before the kernel runs.  Calls whose work overlaps on the GPU (other
- *     streams, other host threads) race on the array: serialise them.
+ *     the call clears the counters and copies the tables, computed on the
+ *     host into static host buffers, on its stream before the kernel runs.
+ *     Calls whose work overlaps on the GPU (other streams, other host
+ *     threads) race on the array: serialise them.
+ *   - Because each call copies its tables from (pageable) host memory, a
+ *     stream that is capturing a graph is refused with INVALID_ARG before
+ *     anything is enqueued, and the capture is left as it was.
  * Errors: INVALID_ARG, UNSUPPORTED_SHAPE, NO_DEVICE, CUDA.
  */
 #define HOUGH_NOALLOC_MAX_THETA 4096

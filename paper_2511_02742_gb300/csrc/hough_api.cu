@@ -72,6 +72,46 @@ namespace {
 // up; checked against the compiled kernel in prepare_find.
 constexpr size_t kStaticSmemReserve = 256;
 
+// Raise a kernel's dynamic shared-memory limit on the current device to at
+// least `bytes`.  The limit belongs to the kernel, not to a context, so it is
+// only ever raised, under a lock: lowering it could fail a launch that
+// another context or host thread is making with more.  The limits set so far
+// are kept in a fixed table (no heap allocation: the allocation-free entry
+// point comes through here too).
+int raise_smem_limit(const void *func, size_t bytes)
+{
+    struct Entry {
+        int dev;
+        const void *func;
+        size_t bytes;
+    };
+    static std::mutex mu;
+    static Entry table[256];
+    static int n_used = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return HOUGH_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    Entry *e = nullptr;
+    for (int i = 0; i < n_used && !e; ++i)
+        if (table[i].dev == dev && table[i].func == func)
+            e = &table[i];
+    if (e && bytes <= e->bytes)
+        return HOUGH_OK;
+    if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return HOUGH_ERR_CUDA;
+    }
+    if (!e && n_used < 256)
+        e = &table[n_used++];
+    if (e)
+        *e = Entry{dev, func, bytes};
+    return HOUGH_OK;
+}
+
 int fail(hough_ctx *ctx, int code)
 {
     if (ctx && code != HOUGH_OK)
@@ -283,8 +323,7 @@ int prepare_find(hough_ctx *ctx, int64_t n_windows, const hough_launch &req, Pre
     if (rc != HOUGH_OK)
         return rc;
     const FindKernel fk = find_kernel_of(ctx);
-    if (cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pr.smem) !=
-        cudaSuccess)
+    if (raise_smem_limit(reinterpret_cast<const void *>(fk), pr.smem) != HOUGH_OK)
         return HOUGH_ERR_CUDA;
     cudaFuncAttributes fa{};
     if (cudaFuncGetAttributes(&fa, fk) != cudaSuccess || fa.sharedSizeBytes > kStaticSmemReserve)
@@ -553,6 +592,9 @@ constexpr size_t kNoAllocBytes =
     kNoAllocCounterBytes + 2 * sizeof(int32_t) * (size_t)HOUGH_NOALLOC_MAX_THETA;
 std::mutex g_noalloc_mutex;
 void *g_noalloc_base[HOUGH_NOALLOC_MAX_DEVICES];   // device address of the array, per device
+// host copies of the tables, written and sent under the mutex (static: the
+// callers this entry point serves may run on small stacks)
+int32_t g_noalloc_C[HOUGH_NOALLOC_MAX_THETA], g_noalloc_S[HOUGH_NOALLOC_MAX_THETA];
 }  // namespace
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
@@ -571,6 +613,16 @@ int hough_find_noalloc(const hough_geometry *g, int n_theta, int n_rho,
     if (n_theta < 1 || n_theta > HOUGH_NOALLOC_MAX_THETA || n_rho < 4 || n_rho > HOUGH_MAX_RHO ||
         n_rho % 4 != 0 || th->max_peaks > HOUGH_MAX_PEAKS)
         return HOUGH_ERR_UNSUPPORTED_SHAPE;
+    cudaStream_t s = (cudaStream_t)stream;
+    // every call copies its tables from host memory, which a stream that is
+    // capturing a graph cannot take: refuse before touching the stream
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return HOUGH_ERR_CUDA;
+    }
+    if (cap != cudaStreamCaptureStatusNone)
+        return HOUGH_ERR_INVALID_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
@@ -580,21 +632,19 @@ int hough_find_noalloc(const hough_geometry *g, int n_theta, int n_rho,
         return HOUGH_ERR_UNSUPPORTED_SHAPE;
     // set-up, once per device, with that device current: the array's name is
     // only a host-side stand-in, so ask the runtime for its device address
-    unsigned char *base = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-        if (!g_noalloc_base[dev]) {
-            void *ptr = nullptr;
-            if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
-                cudaGetLastError();
-                return HOUGH_ERR_CUDA;
-            }
-            g_noalloc_base[dev] = ptr;
+    std::unique_lock<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_base[dev]) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+            cudaGetLastError();
+            return HOUGH_ERR_CUDA;
         }
-        base = static_cast<unsigned char *>(g_noalloc_base[dev]);
+        g_noalloc_base[dev] = ptr;
     }
-    // tables on the host stack (no heap), then into the device array
-    int32_t C[HOUGH_NOALLOC_MAX_THETA], S[HOUGH_NOALLOC_MAX_THETA];
+    unsigned char *base = static_cast<unsigned char *>(g_noalloc_base[dev]);
+    // the tables in the library's static host buffers (held under the mutex
+    // until the copies below have taken them), then into the device array
+    int32_t *C = g_noalloc_C, *S = g_noalloc_S;
     int64_t D = 0;
     int32_t K = 0;
     int rc = hough_tables(g, n_theta, n_rho, C, S, &D, &K);
@@ -622,7 +672,6 @@ int hough_find_noalloc(const hough_geometry *g, int n_theta, int n_rho,
     if (rc != HOUGH_OK)
         return rc;
     ctx.launch = l;
-    cudaStream_t s = (cudaStream_t)stream;
     // the array keeps the last call's contents: the counters must start at 0
     if (cudaMemsetAsync(counter, 0, 2 * sizeof(unsigned int), s) != cudaSuccess ||
         cudaMemcpyAsync(ctx.d_C, C, sizeof(int32_t) * n_theta, cudaMemcpyHostToDevice, s) !=
@@ -632,6 +681,8 @@ int hough_find_noalloc(const hough_geometry *g, int n_theta, int n_rho,
         cudaGetLastError();
         return HOUGH_ERR_CUDA;
     }
+    // a copy from pageable host memory has taken its source when it returns
+    lock.unlock();
     if (n_windows == 0)
         return HOUGH_OK;
     return launch_find(&ctx, hits, window_offsets, n_windows, tracks_out, s, counter, l);
@@ -729,26 +780,32 @@ int hough_accumulate(hough_ctx *ctx, const hough_hits *hits, const int64_t *wind
     // two or more fit on an SM, else one CTA of 1024 threads
     const int word_rows = 32, hit_stage = 2048;
     const size_t smem = hk::align_up((size_t)word_rows * ctx->n_rho * 4, 16) + (size_t)hit_stage * 8;
-    cudaFuncAttributes fa{};
-    if (cudaFuncGetAttributes(&fa, hk::accumulate_kernel) != cudaSuccess)
-        return fail(ctx, HOUGH_ERR_CUDA);
-    if (smem + fa.sharedSizeBytes > ctx->smem_optin)
-        return fail(ctx, HOUGH_ERR_UNSUPPORTED_SHAPE);
-    if (cudaFuncSetAttribute(hk::accumulate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-        return fail(ctx, HOUGH_ERR_CUDA);
-    int threads = 512, occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hk::accumulate_kernel, threads, smem) !=
-        cudaSuccess)
-        return fail(ctx, HOUGH_ERR_CUDA);
-    if (occ < 2) {
-        threads = 1024;
+    if (ctx->acc_threads == 0) {
+        // worked out once per context
+        cudaFuncAttributes fa{};
+        if (cudaFuncGetAttributes(&fa, hk::accumulate_kernel) != cudaSuccess)
+            return fail(ctx, HOUGH_ERR_CUDA);
+        if (smem + fa.sharedSizeBytes > ctx->smem_optin)
+            return fail(ctx, HOUGH_ERR_UNSUPPORTED_SHAPE);
+        if (raise_smem_limit(reinterpret_cast<const void *>(hk::accumulate_kernel), smem) !=
+            HOUGH_OK)
+            return fail(ctx, HOUGH_ERR_CUDA);
+        int threads = 512, occ = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hk::accumulate_kernel, threads,
                                                           smem) != cudaSuccess)
             return fail(ctx, HOUGH_ERR_CUDA);
-        if (occ < 1)
-            return fail(ctx, HOUGH_ERR_UNSUPPORTED_SHAPE);
+        if (occ < 2) {
+            threads = 1024;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hk::accumulate_kernel,
+                                                              threads, smem) != cudaSuccess)
+                return fail(ctx, HOUGH_ERR_CUDA);
+            if (occ < 1)
+                return fail(ctx, HOUGH_ERR_UNSUPPORTED_SHAPE);
+        }
+        ctx->acc_threads = threads;
+        ctx->acc_occ = occ;
     }
+    const int threads = ctx->acc_threads, occ = ctx->acc_occ;
     hough_tracks out{};
     out.acc = acc;
     out.window_status = window_status;
@@ -787,8 +844,7 @@ int hough_find_iterative(hough_ctx *ctx, const hough_hits *hits, const int64_t *
     const size_t smem = (size_t)l.word_rows * ctx->n_rho * 4 + stage;
     if (smem > room)
         return fail(ctx, HOUGH_ERR_UNSUPPORTED_SHAPE);
-    if (cudaFuncSetAttribute(hk::iterative_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
+    if (raise_smem_limit(reinterpret_cast<const void *>(hk::iterative_kernel), smem) != HOUGH_OK)
         return fail(ctx, HOUGH_ERR_CUDA);
     hough_tracks out{};
     out.hit_track = hit_track;
@@ -842,8 +898,7 @@ int hough_extend(hough_ctx *ctx, const hough_hits *hits, const int64_t *window_o
         const size_t smem = hk::ext_smem_bytes(caps[pass], nv);
         if (smem > ctx->smem_optin)
             return fail(ctx, HOUGH_ERR_UNSUPPORTED_SHAPE);
-        if (cudaFuncSetAttribute(hk::extend_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem) != cudaSuccess)
+        if (raise_smem_limit(reinterpret_cast<const void *>(hk::extend_kernel), smem) != HOUGH_OK)
             return fail(ctx, HOUGH_ERR_CUDA);
         int occ = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, hk::extend_kernel, 32, smem) !=

@@ -36,6 +36,9 @@ struct hough_ctx {
     // coarse (18 x 100) and fine (180 x 1000) tables of the two-stage search:
     // C then S of each, on the device; built on first use
     int32_t *d_cf = nullptr;
+    // hough_accumulate's launch (threads per CTA, resident CTAs per SM),
+    // worked out on its first call
+    int acc_threads = 0, acc_occ = 0;
     int cf_K[2] = {0, 0};
     long long cf_D[2] = {0, 0};
 };

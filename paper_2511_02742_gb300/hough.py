@@ -33,6 +33,7 @@ HOUGH_EXT_MAX_VANES = 256
 HOUGH_EXT_MAX_TOL = (1 << 19) - 1
 HOUGH_FLAG_EXPORT_ACC = 1
 HOUGH_FLAG_FP64 = 2
+HOUGH_ERR_INVALID_ARG = -1
 HOUGH_ERR_TIMEOUT = -4
 HOUGH_ERR_UNSUPPORTED_SHAPE = -5
 HOUGH_ERR_BUSY = -7
