@@ -162,7 +162,12 @@ typedef struct hough_tracks {
     int32_t *acc;
 } hough_tracks;
 
-/* Launch shape of the find kernel; 0 in a field means "library default". */
+/*
+ * Launch shape of the find kernel; 0 in a field means "library default".
+ * All fields 0: the first shape that fits of 3 CTAs of 256 threads per SM,
+ * 2 of 512 and 1 of 1024, with 32-word-row tiles (else one CTA of 512
+ * threads with the largest tile that fits).
+ */
 typedef struct hough_launch {
     int32_t threads;      /* threads per CTA: 256, 512 or 1024                     */
     int32_t word_rows;    /* word rows of the shared accumulator tile: 32, 64 or 128   */

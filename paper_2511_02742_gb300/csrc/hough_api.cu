@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstdint>
@@ -25,22 +26,88 @@
 #include "hough_slice.cuh"
 #include "hough_accumulate.cuh"
 
-// Whether every valid hit votes inside [0, n_rho) in every row: the bin is
-// monotone in phi and in z, so the four corners of the detector box bound it.
-static bool box_votes_in_range(const hough_geometry *g, int n_theta, int n_rho, const int32_t *C,
-                               const int32_t *S, long long D, int K)
+// The lowest and highest bin that a hit of the detector box can vote in row
+// t: the bin is monotone in phi and in z, so the box's four corners bound it
+// (phi in [0, 360 deg), z in [z_min, z_min + n_z_strips * pitch], the box the
+// find kernel keeps hits in).
+static void row_reach(const hough_geometry *g, const int32_t *C, const int32_t *S, long long D,
+                      int K, int t, long long &lo, long long &hi)
 {
     const long long phis[2] = {0, 360LL * g->phi_u_per_deg - 1};
     const long long zs[2] = {g->z_min_u, (long long)g->z_min_u + (long long)g->n_z_strips * g->z_pitch_u};
-    for (int t = 0; t < n_theta; ++t)
-        for (long long ph : phis)
-            for (long long z : zs) {
-                const long long v = ph * C[t] + z * S[t] + D;
-                const long long b = v >= 0 ? (v >> K) : -((-v + (1LL << K) - 1) >> K);
-                if (b < 0 || b >= n_rho)
-                    return false;
-            }
+    lo = LLONG_MAX;
+    hi = LLONG_MIN;
+    for (long long ph : phis)
+        for (long long z : zs) {
+            const long long v = ph * C[t] + z * S[t] + D;
+            const long long b = v >= 0 ? (v >> K) : -((-v + (1LL << K) - 1) >> K);
+            lo = std::min(lo, b);
+            hi = std::max(hi, b);
+        }
+}
+
+// Whether every valid hit votes inside [0, n_rho) in every row.
+static bool box_votes_in_range(const hough_geometry *g, int n_theta, int n_rho, const int32_t *C,
+                               const int32_t *S, long long D, int K)
+{
+    for (int t = 0; t < n_theta; ++t) {
+        long long lo, hi;
+        row_reach(g, C, S, D, K, t, lo, hi);
+        if (lo < 0 || hi >= n_rho)
+            return false;
+    }
     return true;
+}
+
+// Narrowed find tiles.  With WR word rows and P counters per word a tile
+// covers rows [k R, (k + 1) R), R = WR P.  Per WR, NB is the widest range of
+// reachable bins inside [0, n_rho) over every tile of every P (rounded up to
+// a multiple of 4), and tile k starts at lo = min(max(lowest reachable bin,
+// 0), n_rho - NB): [lo, lo + NB) then holds every reachable bin of the
+// tile's rows that lies in [0, n_rho), and lies in [0, n_rho) itself, so a
+// vote is inside [0, n_rho) exactly when it is inside the stored bins.  When
+// a bin below 0 is reachable, lo is 0.  lo_all: [WR index][log2 P][tile].
+static void narrow_tiles(hough_ctx *ctx, std::vector<int32_t> &lo_all)
+{
+    const int nt = ctx->n_theta, nr = ctx->n_rho;
+    std::vector<long long> rlo(nt), rhi(nt);
+    for (int t = 0; t < nt; ++t)
+        row_reach(&ctx->g, ctx->C.data(), ctx->S.data(), ctx->D, ctx->K, t, rlo[t], rhi[t]);
+    const int stride = (nt + 31) / 32;
+    ctx->lo_stride = stride;
+    lo_all.assign((size_t)9 * stride, 0);
+    for (int wi = 0; wi < 3; ++wi) {
+        const int WR = 32 << wi;
+        std::vector<long long> tlo((size_t)3 * stride), thi((size_t)3 * stride);
+        long long nb = 4;
+        for (int lp = 0; lp < 3; ++lp) {
+            const int R = WR << lp;
+            for (int k = 0; k * R < nt; ++k) {
+                long long lo = LLONG_MAX, hi = LLONG_MIN;
+                for (int t = k * R; t < std::min(nt, (k + 1) * R); ++t) {
+                    lo = std::min(lo, rlo[t]);
+                    hi = std::max(hi, rhi[t]);
+                }
+                tlo[(size_t)lp * stride + k] = lo;
+                const long long a = std::max(lo, 0LL), b = std::min(hi, (long long)nr - 1);
+                if (b >= a)
+                    nb = std::max(nb, b - a + 1);
+            }
+        }
+        nb = std::min<long long>((nb + 3) & ~3LL, nr);
+        ctx->tile_nb[wi] = (int)nb;
+        for (int lp = 0; lp < 3; ++lp)
+            for (int k = 0; k * (WR << lp) < nt; ++k)
+                lo_all[(size_t)(wi * 3 + lp) * stride + k] = (int32_t)std::min(
+                    std::max(tlo[(size_t)lp * stride + k], 0LL), (long long)nr - nb);
+    }
+}
+
+// Bins a find tile stores per row for this word-row count.
+static int tile_bins(const hough_ctx *ctx, int word_rows)
+{
+    const int wi = word_rows == 32 ? 0 : (word_rows == 64 ? 1 : 2);
+    return ctx->tile_nb[wi] > 0 ? ctx->tile_nb[wi] : ctx->n_rho;
 }
 
 // SM count and shared-memory limits of device dev.
@@ -152,12 +219,13 @@ int cl_entries_for(const hough_ctx *ctx, int word_rows, int hit_stage, int ctas,
     // variables (kStaticSmemReserve covers them): `ctas` CTAs must fit
     const size_t budget = std::min(ctx->smem_optin,
                                    ctx->smem_per_sm / (size_t)ctas - 1024 - kStaticSmemReserve);
-    hk::SmemLayout L0 = hk::smem_layout(word_rows, hit_stage, ctx->n_rho, 0, nw);
+    const int nb = tile_bins(ctx, word_rows);
+    hk::SmemLayout L0 = hk::smem_layout(word_rows, hit_stage, nb, 0, nw);
     long long room = L0.total < budget ? (long long)((budget - L0.total) / 4) : 0;
     // lists able to hold every counter of the tile and of the carried row in
     // their columns, plus the gathered-entry sixth
     const long long need = std::max<long long>(1024, threads + 64LL * nw);
-    const long long worst = (4LL * word_rows * ctx->n_rho + ctx->n_rho) * 12 / 5 + threads;
+    const long long worst = (4LL * word_rows * nb + nb) * 12 / 5 + threads;
     long long n = std::min(room, std::max(worst, need));
     n -= n % (4 * nw);
     if (n < need)
@@ -169,13 +237,16 @@ int cl_entries_for(const hough_ctx *ctx, int word_rows, int hit_stage, int ctas,
 int resolve_launch(const hough_ctx *ctx, const hough_launch &in, hough_launch &out, size_t &smem)
 {
     hough_launch l = in;
-    // Fully default: two CTAs of 512 threads per SM with 32-word-row tiles
-    // when they fit (one CTA's barriers then overlap the other's votes),
-    // else one CTA with the largest tile.
+    // Fully default: the first of these that fits, all with 32-word-row
+    // tiles: three CTAs of 256 threads per SM, two of 512 (several CTAs per
+    // SM overlap one CTA's barriers with the others' votes, and small CTAs
+    // wait less at each barrier), one of 1024; else one CTA of 512 threads
+    // with the largest tile.
     if (l.threads == 0 && l.word_rows == 0 && l.hit_stage == 0 && l.ctas_per_sm == 0) {
-        const hough_launch two{512, 32, 1024, 2};
-        if (resolve_launch(ctx, two, out, smem) == HOUGH_OK)
-            return HOUGH_OK;
+        for (const hough_launch &c : {hough_launch{256, 32, 1024, 3}, hough_launch{512, 32, 1024, 2},
+                                      hough_launch{1024, 32, 2048, 1}})
+            if (resolve_launch(ctx, c, out, smem) == HOUGH_OK)
+                return HOUGH_OK;
     }
     if (l.threads == 0)
         l.threads = 512;
@@ -187,7 +258,8 @@ int resolve_launch(const hough_ctx *ctx, const hough_launch &in, hough_launch &o
         // the largest tile that fits, as long as 16-bit tiles do not pass n_theta
         l.word_rows = 32;
         for (int wr : {128, 64}) {
-            hk::SmemLayout L = hk::smem_layout(wr, l.hit_stage, ctx->n_rho, 4096, l.threads / 32);
+            hk::SmemLayout L = hk::smem_layout(wr, l.hit_stage, tile_bins(ctx, wr), 4096,
+                                               l.threads / 32);
             if ((L.total + 1024 + kStaticSmemReserve) * (size_t)l.ctas_per_sm <= ctx->smem_per_sm &&
                 L.total <= ctx->smem_optin &&
                 ctx->n_theta >= 2 * wr) {
@@ -210,9 +282,10 @@ int resolve_launch(const hough_ctx *ctx, const hough_launch &in, hough_launch &o
     // association keeps one count per warp and category in the tile or in
     // the list area
     const long long cat_counts = (long long)(l.threads / 32) * (ctx->th.max_peaks + 2);
-    if (cat_counts > (long long)l.word_rows * ctx->n_rho && cat_counts > cl)
+    if (cat_counts > (long long)l.word_rows * tile_bins(ctx, l.word_rows) && cat_counts > cl)
         return HOUGH_ERR_UNSUPPORTED_SHAPE;
-    hk::SmemLayout L = hk::smem_layout(l.word_rows, l.hit_stage, ctx->n_rho, cl, l.threads / 32);
+    hk::SmemLayout L = hk::smem_layout(l.word_rows, l.hit_stage, tile_bins(ctx, l.word_rows), cl,
+                                       l.threads / 32);
     if (L.total > ctx->smem_optin)
         return HOUGH_ERR_UNSUPPORTED_SHAPE;
     out = l;
@@ -241,9 +314,11 @@ bool hits_ok(const hough_hits *h)
     return true;
 }
 
+// narrow: the find kernel's narrowed tiles (the other kernels that take these
+// parameters keep full-width tiles)
 hk::KParams make_params(const hough_ctx *ctx, const hough_hits *hits, const int64_t *offsets,
                         int64_t n_windows, const hough_tracks *out, unsigned int *counter,
-                        const hough_launch &l)
+                        const hough_launch &l, bool narrow = true)
 {
     hk::KParams p{};
     const hough_geometry &g = ctx->g;
@@ -288,6 +363,12 @@ hk::KParams make_params(const hough_ctx *ctx, const hough_hits *hits, const int6
     p.work = counter;
     p.word_rows = l.word_rows;
     p.lw = l.word_rows == 32 ? 5 : (l.word_rows == 64 ? 6 : 7);
+    const int wi = p.lw - 5;
+    p.n_b = narrow ? tile_bins(ctx, l.word_rows) : ctx->n_rho;
+    p.lo_tab = narrow && ctx->d_lo ? ctx->d_lo + (size_t)wi * 3 * ctx->lo_stride : nullptr;
+    p.lo_stride = ctx->lo_stride;
+    p.nb_inv = (unsigned)(((1ull << 32) + (unsigned long long)p.n_b - 1) /
+                          (unsigned long long)p.n_b);
     p.nrho_inv = (unsigned)(((1ull << 32) + (unsigned long long)ctx->n_rho - 1) /
                             (unsigned long long)ctx->n_rho);
     p.hit_stage = l.hit_stage;
@@ -486,6 +567,21 @@ int hough_create(const hough_geometry *g, int n_theta, int n_rho, const hough_th
         hough_destroy(ctx);
         return HOUGH_ERR_CUDA;
     }
+    if (!(th->flags & HOUGH_FLAG_FP64)) {
+        // narrowed tiles (the FP64 variant's bins come from another formula,
+        // so its tiles keep every bin)
+        std::vector<int32_t> lo_all;
+        narrow_tiles(ctx, lo_all);
+        if (cudaMalloc(&ctx->d_lo, sizeof(int32_t) * lo_all.size()) != cudaSuccess) {
+            hough_destroy(ctx);
+            return HOUGH_ERR_ALLOC;
+        }
+        if (cudaMemcpy(ctx->d_lo, lo_all.data(), sizeof(int32_t) * lo_all.size(),
+                       cudaMemcpyHostToDevice) != cudaSuccess) {
+            hough_destroy(ctx);
+            return HOUGH_ERR_CUDA;
+        }
+    }
     if (th->flags & HOUGH_FLAG_FP64) {
         // cos and sin of the row centres theta_t = (t + 1/2) pi / n_theta
         std::vector<double> cd(n_theta), sd(n_theta);
@@ -532,6 +628,7 @@ void hough_destroy(hough_ctx *ctx)
     cudaFree(ctx->d_S);
     cudaFree(ctx->d_Cd);
     cudaFree(ctx->d_Sd);
+    cudaFree(ctx->d_lo);
     cudaFree(ctx->stage_dev);
     cudaFree(ctx->d_cf);
     for (int i = 0; i < 2; ++i) {
@@ -810,7 +907,7 @@ int hough_accumulate(hough_ctx *ctx, const hough_hits *hits, const int64_t *wind
     out.acc = acc;
     out.window_status = window_status;
     hough_launch l{threads, word_rows, hit_stage, occ};
-    const hk::KParams p = make_params(ctx, hits, window_offsets, n_windows, &out, nullptr, l);
+    const hk::KParams p = make_params(ctx, hits, window_offsets, n_windows, &out, nullptr, l, false);
     const long long grid = std::min<long long>(n_windows, (long long)ctx->num_sms * occ);
     hk::accumulate_kernel<<<(unsigned)grid, threads, smem, (cudaStream_t)stream>>>(p);
     if (cudaGetLastError() != cudaSuccess)
@@ -850,7 +947,7 @@ int hough_find_iterative(hough_ctx *ctx, const hough_hits *hits, const int64_t *
     out.hit_track = hit_track;
     out.window_status = window_status;
     hk::IterParams q{};
-    q.k = make_params(ctx, hits, window_offsets, n_windows, &out, nullptr, l);
+    q.k = make_params(ctx, hits, window_offsets, n_windows, &out, nullptr, l, false);
     q.max_tracks = max_tracks;
     q.tracks = reinterpret_cast<int4 *>(tracks);
     q.n_tracks = n_tracks;
@@ -883,7 +980,7 @@ int hough_extend(hough_ctx *ctx, const hough_hits *hits, const int64_t *window_o
     hough_tracks f = *found;
     f.window_status = nullptr;
     f.acc = nullptr;
-    q.k = make_params(ctx, hits, window_offsets, n_windows, &f, nullptr, l);
+    q.k = make_params(ctx, hits, window_offsets, n_windows, &f, nullptr, l, false);
     q.n_vanes = nv;
     q.tol_z = tol_z;
     q.ext = reinterpret_cast<int4 *>(out->tracks);
@@ -1227,7 +1324,7 @@ int hough_autotune(hough_ctx *ctx, const hough_hits *hits, const int64_t *window
     float best_ms = 1e30f;
     for (int threads : {256, 512, 1024})
         for (int wr : {32, 64, 128})
-            for (int cps : {1, 2})
+            for (int cps : {1, 2, 3, 4})
                 for (int hs : {1024, 2048}) {
                     hough_launch req{threads, wr, hs, cps};
                     hough_launch l{};

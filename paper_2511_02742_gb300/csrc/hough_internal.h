@@ -19,6 +19,13 @@ struct hough_ctx {
     long long D = 0;
     int K = 0;
     bool in_range = false;   // every valid hit votes inside [0, n_rho) in every row
+    // narrowed find tiles, per launch word-row count 32, 64, 128: the bins a
+    // tile stores per row (0: all n_rho), and on the device the first stored
+    // bin of every tile, [word-row count][log2 P][tile], tile rows lo_stride
+    // apart (null: every tile starts at bin 0)
+    int tile_nb[3] = {0, 0, 0};
+    int32_t *d_lo = nullptr;
+    int lo_stride = 0;
     int32_t *d_C = nullptr, *d_S = nullptr;
     double *d_Cd = nullptr, *d_Sd = nullptr;   // cos/sin of the row centres (HOUGH_FLAG_FP64)
     hough_launch launch{};

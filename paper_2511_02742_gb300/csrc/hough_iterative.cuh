@@ -194,9 +194,9 @@ __device__ unsigned long long iter_best(const KParams &p, uint32_t *acc, const i
             acc4[i] = make_uint4(0u, 0u, 0u, 0u);
         __syncthreads();
         if (p.in_range && t0 + R <= p.n_theta)
-            vote_tile<P, true>(p, acc, stage, nv, t0, nullptr, 0, cnt, none, ws);
+            vote_tile<P, true>(p, acc, stage, nv, t0, 0, nullptr, 0, cnt, none, ws);
         else
-            vote_tile<P, false>(p, acc, stage, nv, t0, nullptr, 0, cnt, none, ws);
+            vote_tile<P, false>(p, acc, stage, nv, t0, 0, nullptr, 0, cnt, none, ws);
         __syncthreads();
         const unsigned long long k = tile_best<P>(p, acc, t0, red);
         if (threadIdx.x == 0) {

@@ -14,22 +14,26 @@
 //
 // Accumulator tile layout.  The tile covers R = WR * P consecutive theta
 // rows.  Its WR "word rows" hold P packed counters per 32-bit word: counter s
-// of word (wr, b) is the count of bin b in tile row s*WR + wr.  P = 4 (8-bit)
-// when the window has <= 255 hits, P = 2 (16-bit) when <= 65535, else P = 1:
-// a count never exceeds the number of hits, so the packed counters are exact.
-// Words are stored bank-private: word (wr, b) lives at
-//     ((wr / 32) * n_rho + b) * 32 + wr % 32,
+// of word (wr, j) is the count of bin lo + j in tile row s*WR + wr.  P = 4
+// (8-bit) when the window has <= 255 hits, P = 2 (16-bit) when <= 65535, else
+// P = 1: a count never exceeds the number of hits, so the packed counters are
+// exact.  A tile stores only NB bins [lo, lo + NB) of each row: the bin is
+// monotone in phi and in z, so the corners of the detector box bound the bins
+// that any hit can reach in a row, and the host gives every tile the first
+// bin lo of a window of NB bins that holds every reachable bin inside
+// [0, n_rho) of its rows (NB about 0.6 n_rho for 128-row tiles over half a
+// turn; NB = n_rho, lo = 0 when no table is given).  Bins outside the window
+// are zero in that tile.  Words are stored bank-private: word (wr, j) lives at
+//     ((wr / 32) * NB + j) * 32 + wr % 32,
 // so every word of word row wr sits in shared-memory bank wr % 32.
 //
 // Voting assigns lane l of a warp to word row 32*g + l and loops the warp over
 // hits; each lane adds one vote per packed row.  Lane l only ever touches bank
 // l, so a warp's vote atomic is always a single conflict-free wavefront,
 // whatever bins the lanes hit (and no two lanes share a word, so no warp
-// aggregation is needed).  The votes use reduction atomics (no return value).
-// The tile is then scanned 16 bytes at a time with a SIMD-within-a-word test
-// for "some counter >= T"; only the indices of the 16-byte groups that pass
-// are listed, and a second pass tests the listed counters for 3x3 local
-// maxima.
+// aggregation is needed).  The vote whose atomic returns T - 1 lists its bin
+// as a candidate (every bin that reaches T is listed exactly once); after the
+// vote the listed bins are tested for 3x3 local maxima.
 //
 // Book-keeping never uses a shared-memory atomic that many warps hit at
 // once (those serialise at tens of cycles each): every warp lists its
@@ -75,6 +79,11 @@ struct KParams {
     int fp64;
     int in_range;       // every valid hit votes inside [0, n_rho) in every row
     int n_theta, n_rho;
+    // narrowed tiles: NB bins stored per row; the first bin of tile k of
+    // counter width P at lo_tab[log2(P) * lo_stride + k] (null: lo = 0)
+    int n_b;
+    const int32_t *lo_tab;
+    int lo_stride;
     int T, tol, max_peaks;
     int export_acc;
     // outputs
@@ -90,7 +99,8 @@ struct KParams {
     // launch shape
     int word_rows;      // WR, 32, 64 or 128
     int lw;             // log2(WR)
-    unsigned nrho_inv;  // ceil(2^32 / n_rho): word-column index -> row group
+    unsigned nb_inv;    // ceil(2^32 / NB): word-column index -> row group
+    unsigned nrho_inv;  // ceil(2^32 / n_rho), the same for full-width tiles
     int hit_stage;      // HS
     int kp;             // top-k region (power of two >= max(32, max_peaks))
     int cl_total;       // entries of the list area (the host sized shared memory with it)
@@ -105,17 +115,18 @@ struct SmemLayout {
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline SmemLayout smem_layout(int word_rows, int hit_stage, int n_rho,
+// n_b: the bins a tile stores per row (NB).
+__host__ __device__ inline SmemLayout smem_layout(int word_rows, int hit_stage, int n_b,
                                                    int cl_entries, int n_warps)
 {
     SmemLayout L;
     size_t off = 0;
     L.acc = off;
-    off = align_up(off + (size_t)word_rows * n_rho * 4, 16);
+    off = align_up(off + (size_t)word_rows * n_b * 4, 16);
     L.stage = off;
     off = align_up(off + (size_t)hit_stage * 8, 16);
     L.carry = off;
-    off = align_up(off + (size_t)2 * n_rho * 4, 16);
+    off = align_up(off + (size_t)2 * n_b * 4, 16);
     L.keys = off;                                   // kept list + one peak segment per warp
     off = align_up(off + (size_t)(HOUGH_MAX_PEAKS + n_warps * kSegPk) * 8, 16);
     L.cl = off;                                     // candidate lists, one per warp
@@ -273,7 +284,8 @@ __device__ __forceinline__ void list_append(uint32_t *seg, int L, int &cnt, cons
 
 template <int P, bool FAST, bool F64 = false>
 __device__ void vote_tile(const KParams &p, uint32_t *acc, const int2 *stage, int nh, int t0,
-                          uint32_t *seg, int L, int &cnt, const ListOvf &ovf, WinScalars &ws)
+                          int lo, uint32_t *seg, int L, int &cnt, const ListOvf &ovf,
+                          WinScalars &ws)
 {
     constexpr int CW = 32 / P;
     constexpr unsigned MASK = P == 1 ? 0xffffffffu : ((1u << CW) - 1u);
@@ -299,11 +311,16 @@ __device__ void vote_tile(const KParams &p, uint32_t *acc, const int2 *stage, in
             cd[k] = sd[k] = 0.0;
         }
     }
-    // bank-private column of this lane: word (wr, b) at col_word0 + 32 b
-    const unsigned col_word0 = (unsigned)(g * p.n_rho) * 32u + (unsigned)lane;
+    // bank-private column of this lane: word (wr, j) at col_word0 + 32 j.
+    // j = b - lo comes straight from the sum with D - lo 2^K: its exact value
+    // lies between 0 and the sum with D for every hit whose bin is >= lo
+    // (and lo = 0 when a bin below 0 is reachable), so it fits in int32 too.
+    const unsigned col_word0 = (unsigned)(g * p.n_b) * 32u + (unsigned)lane;
     const unsigned col = (unsigned)__cvta_generic_to_shared(acc) + 4u * col_word0;
-    const int D = p.D, K = p.K;
-    const unsigned nr = (unsigned)p.n_rho;
+    const int K = p.K;
+    const int D = (int)((unsigned)p.D - ((unsigned)lo << K));
+    // a valid hit's vote is inside [0, n_rho) exactly when j is inside [0, NB)
+    const unsigned nr = (unsigned)p.n_b;
     const unsigned tm1 = (unsigned)(p.T - 1);
     bool oor = false;
     // Software pipelined: the next hit is loaded before this hit's atomics
@@ -326,7 +343,7 @@ __device__ void vote_tile(const KParams &p, uint32_t *acc, const int2 *stage, in
 #pragma unroll
         for (int k = 0; k < P; ++k) {
             if constexpr (F64)
-                bb[k] = rho_bin64(phd, zmm, cd[k], sd[k], p);
+                bb[k] = rho_bin64(phd, zmm, cd[k], sd[k], p) - lo;
             else
                 bb[k] = rho_bin(hv.x, hv.y, c[k], s[k], D, K);
             in[k] = true;
@@ -372,54 +389,44 @@ __device__ __forceinline__ int field(uint32_t w, int s)
     return P == 1 ? (int)w : (int)((w >> (s * CW)) & ((1u << CW) - 1u));
 }
 
-// Shared-memory index of word (wr, b) in the bank-private layout.
-__device__ __forceinline__ int word_index(int wr, int b, int n_rho)
-{
-    return ((wr >> 5) * n_rho + b) * 32 + (wr & 31);
-}
-
-// Value of tile-local row i (0 <= i < WR*P) at bin b.
-template <int P>
-__device__ __forceinline__ int tile_val(const uint32_t *acc, int n_rho, int lw, int i, int b)
-{
-    int s = i >> lw, wr = i & ((1 << lw) - 1);
-    return field<P>(acc[word_index(wr, b, n_rho)], s);
-}
-
 template <int P>
 struct TileView {
     const uint32_t *acc;
     const int *carry0;   // row t0 - 2
     const int *carry1;   // row t0 - 1
-    int t0, R, lw, n_theta, n_rho;
+    int t0, R, lw, n_theta, n_b;
+    int lo;              // first stored bin of this tile
+    int lo_prev;         // first stored bin of the previous tile (the carried rows)
 
-    // Count of (theta row t, rho bin b), 0 outside the accumulator.  Branch
-    // free: the tile word and the carried value are both loaded (with clamped
-    // indices) and the right one is selected, so that the eight loads of a
-    // neighbourhood test are issued together.
+    // Count of (theta row t, rho bin b), 0 outside the accumulator and
+    // outside the stored bins of the row's tile (no vote reaches those).
+    // Branch free: the tile word and the carried value are both loaded (with
+    // clamped indices) and the right one is selected, so that the eight loads
+    // of a neighbourhood test are issued together.
     __device__ __forceinline__ int get(int t, int b) const
     {
         constexpr int CW = 32 / P;
         constexpr unsigned MASK = P == 1 ? 0xffffffffu : ((1u << CW) - 1u);
         const int i = t - t0;
         const int ic = min(max(i, 0), R - 1);
-        const int bc = min(max(b, 0), n_rho - 1);
+        const int jt = b - lo, jc = b - lo_prev;
+        const int jtc = min(max(jt, 0), n_b - 1), jcc = min(max(jc, 0), n_b - 1);
         const int sl = ic >> lw, wr = ic & ((1 << lw) - 1);
-        const uint32_t w = acc[((wr >> 5) * n_rho + bc) * 32 + (wr & 31)];
+        const uint32_t w = acc[((wr >> 5) * n_b + jtc) * 32 + (wr & 31)];
         const int vt = (int)((w >> (sl * CW)) & MASK);
-        const int vc = (i == -2 ? carry0 : carry1)[bc];
+        const int vc = (i == -2 ? carry0 : carry1)[jcc];
         const int v = i >= 0 ? vt : vc;
-        const bool inside = (unsigned)t < (unsigned)n_theta && (unsigned)b < (unsigned)n_rho &&
-                            i >= -2 && i < R;
+        const bool inside = (unsigned)t < (unsigned)n_theta && i >= -2 && i < R &&
+                            (unsigned)(i >= 0 ? jt : jc) < (unsigned)n_b;
         return inside ? v : 0;
     }
 
     // Section 4/5 peak rule: > earlier neighbours (row-major), >= later ones.
     __device__ __forceinline__ bool is_peak(int t, int b, int v) const
     {
-        const int i = t - t0;
-        if (i >= 1 && i + 1 < R && t + 1 < n_theta && b >= 1 && b + 1 < n_rho)
-            return is_peak_inside(i, b, v);
+        const int i = t - t0, j = b - lo;
+        if (i >= 1 && i + 1 < R && t + 1 < n_theta && j >= 1 && j + 1 < n_b)
+            return is_peak_inside(i, j, v);
         const int a0 = get(t - 1, b - 1), a1 = get(t - 1, b), a2 = get(t - 1, b + 1);
         const int a3 = get(t, b - 1), a4 = get(t, b + 1);
         const int a5 = get(t + 1, b - 1), a6 = get(t + 1, b), a7 = get(t + 1, b + 1);
@@ -428,21 +435,22 @@ struct TileView {
         return v > earlier && v >= later;
     }
 
-    // Word index of tile row i at bin b, and the shift of its field.
-    __device__ __forceinline__ int row_word(int i, int b, int &sh) const
+    // Word index of tile row i at stored bin j, and the shift of its field.
+    __device__ __forceinline__ int row_word(int i, int j, int &sh) const
     {
         const int wr = i & ((1 << lw) - 1);
         sh = (i >> lw) * (32 / P);
-        return ((wr >> 5) * n_rho + b) * 32 + (wr & 31);
+        return ((wr >> 5) * n_b + j) * 32 + (wr & 31);
     }
 
-    // The same rule for a bin whose eight neighbours all lie in the tile:
-    // three row bases, then eight plain loads (no clamping or selection).
-    __device__ __forceinline__ bool is_peak_inside(int i, int b, int v) const
+    // The same rule for a bin whose eight neighbours all lie in the tile's
+    // stored bins: three row bases, then eight plain loads (no clamping or
+    // selection).  j is the stored-bin index.
+    __device__ __forceinline__ bool is_peak_inside(int i, int j, int v) const
     {
         constexpr unsigned MASK = P == 1 ? 0xffffffffu : ((1u << (32 / P)) - 1u);
         int sa, sb, sc;
-        const int wa = row_word(i - 1, b, sa), wb = row_word(i, b, sb), wc = row_word(i + 1, b, sc);
+        const int wa = row_word(i - 1, j, sa), wb = row_word(i, j, sb), wc = row_word(i + 1, j, sc);
         const int a0 = (int)((acc[wa - 32] >> sa) & MASK), a1 = (int)((acc[wa] >> sa) & MASK);
         const int a2 = (int)((acc[wa + 32] >> sa) & MASK), a3 = (int)((acc[wb - 32] >> sb) & MASK);
         const int a4 = (int)((acc[wb + 32] >> sb) & MASK), a5 = (int)((acc[wc - 32] >> sc) & MASK);
@@ -547,8 +555,8 @@ __device__ __forceinline__ uint32_t field_flags(uint32_t w, const ScanTest &k)
 }
 
 // Add the bins >= T of the previous tile's last row (carry buffer, evaluated
-// with this tile) to the lanes' columns as 0x80000000 | b; every thread takes
-// every blockDim-th bin.
+// with this tile) to the lanes' columns as 0x80000000 | b (b the bin, stored
+// at carry1[b - lo_prev]); every thread takes every blockDim-th bin.
 template <int P>
 __device__ void list_carry(const KParams &p, const TileView<P> &tv, int rlo, int rhi,
                            uint32_t *seg, int L, int &cnt, const ListOvf &ovf)
@@ -556,9 +564,9 @@ __device__ void list_carry(const KParams &p, const TileView<P> &tv, int rlo, int
     const int tc = tv.t0 - 1;
     if (!(tc >= 0 && tc >= rlo && tc < rhi))
         return;
-    for (int b = threadIdx.x; b < p.n_rho; b += blockDim.x)
-        if (tv.carry1[b] >= p.T)
-            list_append(seg, L, cnt, ovf, 0x80000000u | (unsigned)b);
+    for (int j = threadIdx.x; j < p.n_b; j += blockDim.x)
+        if (tv.carry1[j] >= p.T)
+            list_append(seg, L, cnt, ovf, 0x80000000u | (unsigned)(j + tv.lo_prev));
 }
 
 // Book-keeping of the peaks a warp found in one step (all lanes call): count
@@ -605,12 +613,12 @@ __device__ __forceinline__ void decode_entry(const KParams &p, const TileView<P>
     if (e & 0x80000000u) {
         b = (int)(e & 0xffffu);
         i = -1;
-        v = tv.carry1[b];
+        v = tv.carry1[b - tv.lo_prev];
     } else {
         const int f = (int)(e >> 2), s = (int)(e & 3u);
-        const int qq = f >> 5;                                     // g * n_rho + b
-        const int g = (int)__umulhi((unsigned)qq, p.nrho_inv);
-        b = qq - g * p.n_rho;
+        const int qq = f >> 5;                                     // g * NB + j
+        const int g = (int)__umulhi((unsigned)qq, p.nb_inv);
+        b = qq - g * p.n_b + tv.lo;
         i = s * p.word_rows + g * 32 + (f & 31);
         v = (int)((tv.acc[f] >> (s * CW)) & MASK);
     }
@@ -782,7 +790,8 @@ __device__ void merge_peaks(const KParams &p, unsigned long long *keys,
 // 32-byte sector (two 16-byte stores).  When the accumulator is not 16-byte
 // aligned the same values go out as plain 4-byte stores.
 template <int P>
-__device__ void export_tile(const KParams &p, const uint32_t *acc, int t0, int R, long long w)
+__device__ void export_tile(const KParams &p, const uint32_t *acc, int t0, int R, int lo,
+                            long long w)
 {
     constexpr int CW = 32 / P;
     constexpr unsigned MASK = P == 1 ? 0xffffffffu : ((1u << CW) - 1u);
@@ -795,11 +804,12 @@ __device__ void export_tile(const KParams &p, const uint32_t *acc, int t0, int R
         const int g = item / nq, b0 = (item - g * nq) * 8;
         const int wr = g * 32 + lane;
         const int nb = min(8, p.n_rho - b0);            // 8, or 4 at a ragged end
-        const uint32_t *col = acc + (size_t)(g * p.n_rho + b0) * 32 + lane;
+        const int j0 = b0 - lo;                         // bins outside [lo, lo + NB) are 0
         uint32_t wv[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j)
-            wv[j] = j < nb ? col[j * 32] : 0u;
+            wv[j] = (j < nb && (unsigned)(j0 + j) < (unsigned)p.n_b)
+                        ? acc[(size_t)(g * p.n_b + j0 + j) * 32 + lane] : 0u;
 #pragma unroll
         for (int s = 0; s < P; ++s) {
             const int t = t0 + s * WR + wr;
@@ -857,15 +867,15 @@ __device__ void check_direct(const KParams &p, const TileView<P> &tv, int rlo, i
 // End of a tile: zero the tile after its last read and, when another tile
 // follows, first save its last two rows (tile rows R-2 and R-1, field P-1 of
 // word rows WR-2 and WR-1, i.e. words 30 and 31 of the 16-byte chunk
-// ((G-1) n_rho + b) * 8 + 7) as the carried rows of the next tile.  The
-// thread that saves a chunk's words is the one that zeroes the chunk, so no
-// barrier separates the two.
+// ((G-1) NB + j) * 8 + 7) as the carried rows of the next tile (stored bin j
+// of this tile at carry[j]).  The thread that saves a chunk's words is the
+// one that zeroes the chunk, so no barrier separates the two.
 template <int P>
 __device__ void tile_end(const KParams &p, uint32_t *acc, int *carry0, int *carry1, bool save)
 {
     const int G = p.word_rows >> 5;
-    const int n4 = (p.word_rows * p.n_rho) >> 2;
-    const int c0 = 8 * (G - 1) * p.n_rho;
+    const int n4 = (p.word_rows * p.n_b) >> 2;
+    const int c0 = 8 * (G - 1) * p.n_b;
     uint4 *acc4 = reinterpret_cast<uint4 *>(acc);
     for (int i = threadIdx.x; i < n4; i += blockDim.x) {
         if (save && i >= c0 && (i & 7) == 7) {
@@ -953,7 +963,10 @@ __device__ int process_tiles(const KParams &p, long long beg, int H, uint32_t *a
     const bool single = H <= p.hit_stage;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int seg_cap = kSegPk;
-    int *carry0 = carry, *carry1 = carry + p.n_rho;
+    int *carry0 = carry, *carry1 = carry + p.n_b;
+    constexpr int lgP = P == 4 ? 2 : (P == 2 ? 1 : 0);
+    const int32_t *lo_row = p.lo_tab ? p.lo_tab + lgP * p.lo_stride : nullptr;
+    int lo_prev = 0;
     uint32_t *my_cl = cl + (size_t)warp * p.seg_cl;
     const int L = (p.seg_cl - p.seg_ovf) >> 5;      // column slots per lane
     const ListOvf ovf{wc.n_ovf + warp, p.seg_ovf};
@@ -967,20 +980,21 @@ __device__ int process_tiles(const KParams &p, long long beg, int H, uint32_t *a
         const bool last = tile == n_tiles - 1;
         int cnt = 0;        // this lane's column entries (a register)
         const bool fast = !F64 && p.in_range && t0 + R <= p.n_theta;
-        TileView<P> tv{acc, carry0, carry1, t0, R, p.lw, p.n_theta, p.n_rho};
+        const int lo = lo_row ? __ldg(lo_row + tile) : 0;
+        TileView<P> tv{acc, carry0, carry1, t0, R, p.lw, p.n_theta, p.n_b, lo, lo_prev};
         const int rlo = max(t0 - 1, 0);
         const int rhi = last ? p.n_theta : t0 + R - 1;
         const int ihi = rhi - t0;
         if (single) {
             if (fast)
-                vote_tile<P, !F64, F64>(p, acc, stage, nv, t0, my_cl, L, cnt, ovf, ws);
+                vote_tile<P, !F64, F64>(p, acc, stage, nv, t0, lo, my_cl, L, cnt, ovf, ws);
             else
-                vote_tile<P, false, F64>(p, acc, stage, nv, t0, my_cl, L, cnt, ovf, ws);
+                vote_tile<P, false, F64>(p, acc, stage, nv, t0, lo, my_cl, L, cnt, ovf, ws);
         } else {
             for (long long s0 = 0; s0 < H; s0 += p.hit_stage) {
                 int n = (int)min((long long)p.hit_stage, (long long)H - s0);
                 int ns = stage_hits(p, beg + s0, n, stage, wtot, ws);
-                vote_tile<P, false, F64>(p, acc, stage, ns, t0, my_cl, L, cnt, ovf, ws);
+                vote_tile<P, false, F64>(p, acc, stage, ns, t0, lo, my_cl, L, cnt, ovf, ws);
                 __syncthreads();
             }
         }
@@ -992,7 +1006,7 @@ __device__ int process_tiles(const KParams &p, long long beg, int H, uint32_t *a
         // sends the tile to the direct test of every counter.
         const bool lost = __syncthreads_or(lane == 0 && *ovf.count > p.seg_ovf);
         if (p.export_acc)
-            export_tile<P>(p, acc, t0, R, w);
+            export_tile<P>(p, acc, t0, R, lo, w);
         PeakSink ps{keys + p.kp + (size_t)warp * seg_cap, seg_cap, wc.n_pk[warp], 0, ws.kth,
                     ws.vk, vh + warp * kHistBins};
         if (!lost)
@@ -1006,6 +1020,7 @@ __device__ int process_tiles(const KParams &p, long long beg, int H, uint32_t *a
         // every check step ended in a barrier, so neither the tile nor the
         // carried rows are read any more
         tile_end<P>(p, acc, carry0, carry1, !last);
+        lo_prev = lo;
         if (threadIdx.x < 32)
             wc.n_ovf[threadIdx.x] = 0;
         __syncthreads();
@@ -1249,7 +1264,7 @@ __global__ void __launch_bounds__(1024, 1) find_kernel(KParams p)
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ WinScalars ws;
     const int nw = blockDim.x >> 5;
-    const SmemLayout L = smem_layout(p.word_rows, p.hit_stage, p.n_rho, p.cl_total, nw);
+    const SmemLayout L = smem_layout(p.word_rows, p.hit_stage, p.n_b, p.cl_total, nw);
     uint32_t *acc = reinterpret_cast<uint32_t *>(smem + L.acc);
     int2 *stage = reinterpret_cast<int2 *>(smem + L.stage);
     int *carry = reinterpret_cast<int *>(smem + L.carry);
@@ -1266,7 +1281,7 @@ __global__ void __launch_bounds__(1024, 1) find_kernel(KParams p)
     // the tile starts all zero; every tile and the association leave it so
     {
         uint4 *acc4 = reinterpret_cast<uint4 *>(acc);
-        for (int i = threadIdx.x; i < (p.word_rows * p.n_rho) >> 2; i += blockDim.x)
+        for (int i = threadIdx.x; i < (p.word_rows * p.n_b) >> 2; i += blockDim.x)
             acc4[i] = make_uint4(0u, 0u, 0u, 0u);
     }
     long long w = blockIdx.x;
@@ -1323,7 +1338,7 @@ __global__ void __launch_bounds__(1024, 1) find_kernel(KParams p)
             // area when they fit
             int *wcat, *cat_s;
             const int need = nw * (n_top + 2);
-            if (need <= p.word_rows * p.n_rho) {
+            if (need <= p.word_rows * p.n_b) {
                 wcat = reinterpret_cast<int *>(acc);
                 cat_s = H <= p.cl_total ? reinterpret_cast<int *>(cl) : nullptr;
             } else {

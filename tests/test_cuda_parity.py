@@ -192,15 +192,75 @@ def test_launch_shapes_identical(hough):
     w = synth.generate(300, ("poisson", 10, 1, 40), (100.0, 300.0), 0.02, seed=9)
     f = _finder(hough, 512, 512)
     base = gpu_run(f, w)
-    for threads in (256, 512, 1024):
-        for wr in (32, 64):
-            for hs in (256, 2048):
-                hough.hough_set_launch(f.ctx, threads, wr, hs, 1)
-                g = gpu_run(f, w)
-                for k in ("n_peaks", "n_found", "status", "hit_track", "track_hits"):
-                    np.testing.assert_array_equal(g[k], base[k], err_msg=f"{k} {threads} {wr} {hs}")
-                np.testing.assert_array_equal(g["peaks"], base["peaks"])
+    shapes = [(t, wr, hs, 1) for t in (256, 512, 1024) for wr in (32, 64) for hs in (256, 2048)]
+    shapes += [(256, 32, 1024, 3), (256, 32, 512, 3), (512, 32, 1024, 2), (256, 64, 512, 2)]
+    for shape in shapes:
+        hough.hough_set_launch(f.ctx, *shape)
+        g = gpu_run(f, w)
+        for k in ("n_peaks", "n_found", "status", "hit_track", "track_hits"):
+            np.testing.assert_array_equal(g[k], base[k], err_msg=f"{k} {shape}")
+        np.testing.assert_array_equal(g["peaks"], base["peaks"])
     f.close()
+
+
+def test_narrowed_tiles_at_reach_edges(hough):
+    """A tile stores only the bins that hits of the detector box can reach in
+    its rows; the box's corners reach the extreme bins.  Stacks of hits at
+    the four corners and hits along the box's edges (encoded, so the corners
+    are exact), at several accumulator shapes and launch shapes (1 to 3 CTAs
+    per SM, 32 to 128 word rows, a streamed stage): peaks, associations and the
+    exported accumulator (zero outside the reachable bins) equal the
+    oracle's."""
+    import torch
+    rng = np.random.default_rng(21)
+    phi_hi = 360 * G["phi_u_per_deg"] - 1
+    z_lo = G["z_min_u"]
+    z_hi = G["z_min_u"] + G["n_z_strips"] * G["z_pitch_u"]
+    corners = [(0, z_lo), (0, z_hi), (phi_hi, z_lo), (phi_hi, z_hi)]
+
+    def stack(pts, n):
+        return [p for p in pts for _ in range(n)]
+
+    edge_phi = rng.integers(0, phi_hi + 1, 40)
+    edge_z = rng.integers(z_lo, z_hi + 1, 40)
+    wins = [
+        stack(corners, 12),
+        stack(corners[:1], 6) + stack(corners[3:], 9)
+        + list(zip(rng.integers(0, phi_hi + 1, 50), rng.integers(z_lo, z_hi + 1, 50))),
+        [(0, z) for z in edge_z] + [(p, z_hi) for p in edge_phi] + stack(corners[1:3], 7),
+        stack(corners, 60) + [(p, z_lo) for p in edge_phi] + [(phi_hi, z) for z in edge_z],
+        stack(corners, 5) + [(phi_hi + 1, 0), (0, z_hi + 1)],
+    ]
+    phi = np.array([p for wn in wins for p, _ in wn], np.int32)
+    z = np.array([q for wn in wins for _, q in wn], np.int32)
+    off = np.zeros(len(wins) + 1, np.int64)
+    off[1:] = np.cumsum([len(wn) for wn in wins])
+    assert off[4] - off[3] > 255                        # one window with 16-bit counters
+    hits = dict(phi_q=torch.from_numpy(phi).cuda(), z_q=torch.from_numpy(z).cuda())
+    offs = torch.from_numpy(off).cuda()
+    launches = [None, (256, 32, 1024, 3), (512, 32, 1024, 2), (1024, 32, 2048, 1),
+                (512, 64, 1024, 1), (512, 128, 1024, 1), (256, 32, 256, 1)]
+    for n_theta, n_rho in [(512, 512), (1024, 1024), (180, 1000), (97, 332), (128, 512), (33, 64)]:
+        ref = oracle.find_batch(G, n_theta, n_rho, phi, z, off, export_acc=True)
+        assert ref["status"][4] & hough.HOUGH_WIN_HIT_OUT_OF_RANGE
+        f = _finder(hough, n_theta, n_rho, export_acc=True)
+        ran = 0
+        for lch in launches:
+            if lch is not None:
+                try:
+                    hough.hough_set_launch(f.ctx, *lch)
+                except hough.HoughError as e:
+                    assert e.code == hough.HOUGH_ERR_UNSUPPORTED_SHAPE
+                    continue
+            out = f.find(hits, offs)
+            torch.cuda.synchronize()
+            g = to_numpy(out, len(phi))
+            wn = synth.Windows(phi, z, off, np.zeros(len(phi), np.int32), np.zeros(len(phi)),
+                               np.zeros((0, 4)), np.zeros(len(wins) + 1, np.int64))
+            assert_batch_equal(g, ref, wn, check_acc=True)
+            ran += 1
+        assert ran >= 3, (n_theta, n_rho, ran)
+        f.close()
 
 
 def test_alone_vs_batch_and_repeat(hough):
