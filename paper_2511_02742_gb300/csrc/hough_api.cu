@@ -391,9 +391,12 @@ struct Prepared {
 
 // The find kernel of a context: fixed-point bins, or the FP64 variant.
 using FindKernel = void (*)(hk::KParams);
-static FindKernel find_kernel_of(const hough_ctx *ctx)
+// The find kernel for this context and CTA size.
+static FindKernel find_kernel_of(const hough_ctx *ctx, int threads)
 {
-    return (ctx->th.flags & HOUGH_FLAG_FP64) ? hk::find_kernel<true> : hk::find_kernel<false>;
+    if (ctx->th.flags & HOUGH_FLAG_FP64)
+        return hk::find_kernel<true>;
+    return threads <= 256 ? hk::find_kernel_256 : hk::find_kernel<false>;
 }
 
 // Resolve a launch shape, raise the kernel's shared-memory limit and size the
@@ -403,7 +406,7 @@ int prepare_find(hough_ctx *ctx, int64_t n_windows, const hough_launch &req, Pre
     int rc = resolve_launch(ctx, req, pr.l, pr.smem);
     if (rc != HOUGH_OK)
         return rc;
-    const FindKernel fk = find_kernel_of(ctx);
+    const FindKernel fk = find_kernel_of(ctx, pr.l.threads);
     if (raise_smem_limit(reinterpret_cast<const void *>(fk), pr.smem) != HOUGH_OK)
         return HOUGH_ERR_CUDA;
     cudaFuncAttributes fa{};
@@ -424,7 +427,7 @@ int enqueue_find(hough_ctx *ctx, const hough_hits *hits, const int64_t *offsets,
                  unsigned int *counter, const Prepared &pr)
 {
     hk::KParams p = make_params(ctx, hits, offsets, n_windows, out, counter, pr.l);
-    find_kernel_of(ctx)<<<pr.grid, pr.l.threads, pr.smem, s>>>(p);
+    find_kernel_of(ctx, pr.l.threads)<<<pr.grid, pr.l.threads, pr.smem, s>>>(p);
     if (cudaGetLastError() != cudaSuccess)
         return HOUGH_ERR_CUDA;
     ctx->launches += 1;
