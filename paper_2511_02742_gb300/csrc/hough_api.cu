@@ -243,7 +243,7 @@ int resolve_launch(const hough_ctx *ctx, const hough_launch &in, hough_launch &o
     // wait less at each barrier), one of 1024; else one CTA of 512 threads
     // with the largest tile.
     if (l.threads == 0 && l.word_rows == 0 && l.hit_stage == 0 && l.ctas_per_sm == 0) {
-        for (const hough_launch &c : {hough_launch{256, 32, 1024, 3}, hough_launch{512, 32, 1024, 2},
+        for (const hough_launch &c : {hough_launch{256, 32, 512, 3}, hough_launch{512, 32, 1024, 2},
                                       hough_launch{1024, 32, 2048, 1}})
             if (resolve_launch(ctx, c, out, smem) == HOUGH_OK)
                 return HOUGH_OK;

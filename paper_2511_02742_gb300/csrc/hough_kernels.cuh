@@ -48,7 +48,7 @@
 
 namespace hk {
 
-constexpr int kSegPk = 64;      // peak-key segment per warp; merged when past 32 entries
+constexpr int kSegPk = 128;     // peak-key segment per warp; merged when past 96 entries
 constexpr int kSegRoom = 32;    // appends one check step can make per warp (1 per lane)
 constexpr int kMergeStage = 4 * HOUGH_MAX_PEAKS * 4 / 8;   // merge staging keys (the pk area)
 constexpr unsigned long long kKeyMax = ~0ull;
@@ -328,7 +328,7 @@ __device__ void vote_tile(const KParams &p, uint32_t *acc, const int2 *stage, in
     // are issued before any returned value is tested.
     int h = warp / G;
     int2 nxt = stage[max(min(h, nh - 1), 0)];
-#pragma unroll 2
+#pragma unroll 4
     for (; h < nh; h += hstep) {
         const int2 hv = nxt;
         nxt = stage[min(h + hstep, nh - 1)];
