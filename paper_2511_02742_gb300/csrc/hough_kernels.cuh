@@ -834,33 +834,66 @@ __device__ void export_tile(const KParams &p, const uint32_t *acc, int t0, int R
     }
 }
 
-// Direct test of every counter of the evaluable rows: used only when a
-// tile holds more candidate bins than the lists (adversarial inputs).
+// Direct test of every counter of the evaluable rows, used when a tile holds
+// more candidate bins than the lists (an overflow area overflowed).  Warp
+// local, like the list test: the work items are the carried row's stored bins
+// in groups of 32 (when that row is evaluated with this tile), then every word
+// column (g, j) of the tile with one word row per lane (so a warp's loads hit
+// 32 different banks); items are dealt to the warps in turn.  A word column
+// whose 32 words hold no counter >= T (one SWAR test per word) costs one load
+// and one vote; otherwise its P fields are tested one step each.  A warp
+// stops while its peak segment lacks room for 32 more keys; the block barrier
+// that ends the round merges the segments and the warps go on.  Every warp
+// leaves through the same barrier.
 template <int P>
 __device__ void check_direct(const KParams &p, const TileView<P> &tv, int rlo, int rhi,
                              PeakSink &ps, unsigned long long *keys, unsigned long long *top_stage,
-                             int seg_cap, WarpCounters wc, const int *vh, WinScalars &ws)
+                             WarpCounters wc, const int *vh, WinScalars &ws)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int ilo = max(rlo - tv.t0, -1), ihi = min(rhi - tv.t0, tv.R);
-    const int nrows = ihi - ilo;
-    const long long total = (long long)nrows * p.n_rho;
-    for (long long x0 = 0; x0 < total; x0 += blockDim.x) {
-        const long long x = x0 + threadIdx.x;
-        const int i = ilo + (int)(x / p.n_rho);
-        const int b = (int)(x % p.n_rho);
-        const int t = tv.t0 + i;
-        const int v = x < total ? tv.get(t, b) : 0;
-        const bool peak = x < total && t >= rlo && v >= p.T && tv.is_peak(t, b, v);
-        record_peaks(peak, v, t, b, ps);
+    const int G = p.word_rows >> 5;
+    const ScanTest k = make_test<P>(p.T);
+    const int n_carry = ilo < 0 ? (p.n_b + 31) >> 5 : 0;
+    const int n_items = n_carry + G * p.n_b;
+    int x = warp, s0 = 0;     // this warp's next item and, in a word column, its next field
+    for (;;) {
+        while (x < n_items && ps.n <= kSegPk - kSegRoom) {
+            if (x < n_carry) {
+                const int j = x * 32 + lane;
+                const int v = j < p.n_b ? tv.carry1[j] : 0;
+                const int b = tv.lo_prev + j;
+                const bool peak = v >= p.T && tv.is_peak(tv.t0 - 1, b, v);
+                record_peaks(peak, v, tv.t0 - 1, b, ps);
+                x += nw;
+                continue;
+            }
+            const int q = x - n_carry;                          // g * NB + j
+            const int g = (int)__umulhi((unsigned)q, p.nb_inv);
+            const int j = q - g * p.n_b;
+            const uint32_t wv = tv.acc[q * 32 + lane];
+            if (s0 == 0 && __ballot_sync(0xffffffffu, word_has<P>(wv, k)) == 0u) {
+                x += nw;
+                continue;
+            }
+            const int i = s0 * p.word_rows + g * 32 + lane;
+            const int v = field<P>(wv, s0);
+            const int b = tv.lo + j;
+            const bool peak = i < ihi && v >= p.T && tv.is_peak(tv.t0 + i, b, v);
+            record_peaks(peak, v, tv.t0 + i, b, ps);
+            if (++s0 == P) {
+                s0 = 0;
+                x += nw;
+            }
+        }
         if (lane == 0)
             wc.n_pk[warp] = ps.n;
-        if (__syncthreads_or(lane == 0 && ps.n > ps.cap - kSegRoom)) {
-            merge_peaks(p, keys, top_stage, seg_cap, wc, vh, ws);
-            ps.n = 0;
-            ps.kth = ws.kth;
-            ps.vk = ws.vk;
-        }
+        if (!__syncthreads_or(lane == 0 && x < n_items))
+            break;
+        merge_peaks(p, keys, top_stage, kSegPk, wc, vh, ws);
+        ps.n = 0;
+        ps.kth = ws.kth;
+        ps.vk = ws.vk;
     }
 }
 
@@ -1012,7 +1045,7 @@ __device__ int process_tiles(const KParams &p, long long beg, int H, uint32_t *a
         if (!lost)
             check_lists<P>(p, tv, ihi, my_cl, L, cnt, *ovf.count, ps, keys, top_stage, wc, vh, ws);
         else
-            check_direct<P>(p, tv, rlo, rhi, ps, keys, top_stage, seg_cap, wc, vh, ws);
+            check_direct<P>(p, tv, rlo, rhi, ps, keys, top_stage, wc, vh, ws);
         if (lane == 0) {
             wc.n_pk[warp] = ps.n;
             wc.n_found[warp] += ps.found;

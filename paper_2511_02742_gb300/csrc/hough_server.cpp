@@ -107,6 +107,11 @@ struct hough_server {
     hough_ctx *ctx = nullptr;
     hough_server_config cfg{};
     hough_launch saved_launch{};     // the context's shape before the server
+    // shapes chosen per batch when the configuration leaves the shape open:
+    // the latency shape for batches of fewer than 2 windows per SM, else the
+    // context's default (throughput) shape
+    bool per_batch = false;
+    hough_launch lat_launch{}, thr_launch{};
     int max_peaks = 0;
     size_t in_cap = 0, out_cap = 0, stage_cap = 0;
     std::vector<Slot> slots;
@@ -184,6 +189,8 @@ int launch_slot(hough_server *s, Slot &sl)
     t.window_status = reinterpret_cast<uint32_t *>(sl.d_out + O.st);
     t.hit_track = reinterpret_cast<int32_t *>(sl.d_out + O.ht);
     t.track_hits = reinterpret_cast<int32_t *>(sl.d_out + O.th);
+    if (s->per_batch)
+        s->ctx->launch = sl.W >= 2 * (int64_t)s->ctx->num_sms ? s->thr_launch : s->lat_launch;
     int rc = hough_find(s->ctx, &hits, reinterpret_cast<const int64_t *>(sl.d_in + L.off), sl.W,
                         &t, sl.stream);
     if (rc != HOUGH_OK)
@@ -385,13 +392,29 @@ int hough_server_create(hough_ctx *ctx, const hough_server_config *cfg, hough_se
     s->ctx = ctx;
     s->cfg = *cfg;
     s->max_peaks = ctx->th.max_peaks;
-    // the server's launch shape: as given, else one CTA of 1024 threads per
-    // SM with the largest tile (small batches then spread over every SM, and
-    // each window has the most warps)
+    // the server's launch shape: as given, else chosen per batch: one CTA of
+    // 1024 threads per SM with 32-word-row tiles for small batches (they then
+    // spread over every SM, and each window has the most warps), the
+    // context's default shape (several CTAs per SM, the highest throughput)
+    // for batches of at least two windows per SM
     s->saved_launch = ctx->launch;
     hough_launch want = cfg->launch;
-    if (want.threads == 0 && want.word_rows == 0 && want.hit_stage == 0 && want.ctas_per_sm == 0)
-        want = hough_launch{1024, 0, 2048, 1};
+    if (want.threads == 0 && want.word_rows == 0 && want.hit_stage == 0 && want.ctas_per_sm == 0) {
+        const hough_launch def{}, lat{1024, 32, 2048, 1};
+        if (hough_set_launch(ctx, &def) != HOUGH_OK) {
+            ctx->launch = s->saved_launch;
+            delete s;
+            cudaSetDevice(prev);
+            return HOUGH_ERR_INVALID_ARG;
+        }
+        s->thr_launch = ctx->launch;
+        want = lat;
+        if (hough_set_launch(ctx, &want) != HOUGH_OK)
+            want = s->thr_launch;       // no room for the latency shape: one shape
+        else
+            s->per_batch = true;
+        s->lat_launch = ctx->launch;
+    }
     if (hough_set_launch(ctx, &want) != HOUGH_OK) {
         ctx->launch = s->saved_launch;
         delete s;

@@ -161,12 +161,37 @@ def test_peak_overflow_and_candidate_buffer_fallback(hough):
     parts = [(rng.integers(0, 40, 2000), rng.integers(0, 2048, 2000)) for _ in range(3)]
     w = _windows_from_arrays(parts)
     for mp in (256, 7, 0):
-        f = _finder(hough, 256, 1024, vote_threshold=1, max_peaks=mp)
-        g = gpu_run(f, w)
         ref = oracle_run(w, 256, 1024, vote_threshold=1, max_peaks=mp)
         assert ref["n_found"].min() > 3000
-        assert_batch_equal(g, ref, w)
+        f = _finder(hough, 256, 1024, vote_threshold=1, max_peaks=mp)
+        ran = 0
+        for lch in (None, (256, 32, 512, 3), (512, 32, 1024, 2), (1024, 32, 2048, 1),
+                    (512, 32, 1024, 1), (256, 32, 256, 1)):
+            if lch is not None:
+                try:
+                    hough.hough_set_launch(f.ctx, *lch)
+                except hough.HoughError as e:
+                    assert e.code == hough.HOUGH_ERR_UNSUPPORTED_SHAPE
+                    continue
+            assert_batch_equal(gpu_run(f, w), ref, w)
+            ran += 1
+        assert ran >= 3
         f.close()
+
+
+def test_heavy_windows_in_small_ctas(hough):
+    """Windows of 1 to 40 tracks (about 300 hits, half of them past the 8-bit
+    limit) in three 256-thread CTAs per SM: the lists of some tiles overflow
+    and those tiles take the direct test of every stored counter.  Equal to
+    the oracle, in that shape and in larger ones."""
+    cfg = synth.WORKLOADS["serving"]
+    w = synth.workload("serving", n_windows=240, seed=4)
+    ref = oracle_run(w, cfg["n_theta"], cfg["n_rho"])
+    f = _finder(hough, cfg["n_theta"], cfg["n_rho"])
+    for lch in ((256, 32, 512, 3), (256, 32, 1024, 3), (512, 32, 1024, 2), (1024, 32, 2048, 1)):
+        hough.hough_set_launch(f.ctx, *lch)
+        assert_batch_equal(gpu_run(f, w), ref, w)
+    f.close()
 
 
 def test_bad_offsets_are_flagged_not_read(hough):

@@ -227,3 +227,33 @@ def test_pageable_request_buffers():
         _check(ref, w, a, b, {k: torch.from_numpy(v) for k, v in out.items()}, f.max_peaks)
     srv.close()
     f.close()
+
+
+def test_small_and_large_batches_under_the_default_shapes():
+    """With the launch shape left open the server runs a batch of fewer than
+    two windows per SM with one 1024-thread CTA per SM and a larger one with
+    the context's default shape; both give the bits hough_find gives, and the
+    context's own shape is back after the server is closed."""
+    import torch
+    from paper_2511_02742_gb300 import hough
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    cfg = synth.WORKLOADS["serving"]
+    w = synth.workload("serving", n_windows=4 * sms + 200, seed=12)
+    f = hough.Finder(cfg["n_theta"], cfg["n_rho"])
+    hough.hough_set_launch(f.ctx, 512, 32, 1024, 2)
+    before = hough.hough_get_launch(f.ctx)
+    ref = _reference(hough, f, w)
+    srv = hough.Server(f, n_slots=2, slot_windows=4 * sms + 200, slot_hits=1 << 21)
+    try:
+        jobs = []
+        for a, b in [(0, 10), (10, 10 + 2 * sms + 50), (10 + 2 * sms + 50, 4 * sms + 200),
+                     (5, 2 * sms + 4)]:
+            out = _host_out(f, b - a, int(w.offsets[b] - w.offsets[a]))
+            jobs.append((a, b, out, _submit(srv, w, a, b, out)))
+            assert srv.wait(jobs[-1][3], 60000)["status"] == 0     # one request per batch
+        for a, b, out, _ in jobs:
+            _check(ref, w, a, b, out, f.max_peaks)
+    finally:
+        srv.close()
+    assert hough.hough_get_launch(f.ctx) == before
+    f.close()
