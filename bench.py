@@ -611,6 +611,15 @@ def _serving_leg(args, dev):
     n_theta, n_rho = cfg["n_theta"], cfg["n_rho"]
     pool = _workload("serving", args.serve_pool, 4242)
     f = hough.Finder(n_theta, n_rho)
+    tuned = None
+    if args.autotune:
+        # the throughput shape of the server's large batches: autotuned on
+        # the first 2000 windows of the pool
+        sub = pool.subset(np.arange(min(pool.n_windows, 2000)))
+        sh = dict(vane=torch.from_numpy(sub.vane).to(dev), strip=torch.from_numpy(sub.strip).to(dev))
+        so = torch.from_numpy(sub.offsets).to(dev)
+        tuned = f.autotune(sh, so, f.alloc_outputs(sub.n_windows, sub.n_hits, device=dev), iters=2)
+        del sh, so
     ref = f.find(dict(vane=torch.from_numpy(pool.vane).to(dev),
                       strip=torch.from_numpy(pool.strip).to(dev)),
                  torch.from_numpy(pool.offsets).to(dev))
@@ -622,8 +631,9 @@ def _serving_leg(args, dev):
            f.alloc_outputs(pool.n_windows, pool.n_hits, device="cpu", pin=True).items()}
     launch = [int(x) for x in args.serve_launch.split(",")] if args.serve_launch else None
     launch_used = (dict(zip(("threads", "word_rows", "hit_stage", "ctas_per_sm"), launch))
-                   if launch else "server default: 1024 threads, 1 CTA per SM, largest tile, "
-                                  "2048-hit stage")
+                   if launch else {"below 2 windows per SM": "1024 threads, 1 CTA per SM, 32 "
+                                   "word rows, 2048-hit stage",
+                                   "from 2 windows per SM": tuned or hough.hough_get_launch(f.ctx)})
     srv = hough.Server(f, n_slots=4, slot_windows=4096, slot_hits=1 << 21, max_queued=1 << 16,
                        launch=launch)
     base = _serve_point(srv, pool, ref, out, vane, strip, args.serve_rate, args.serve_seconds,

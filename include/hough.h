@@ -524,10 +524,14 @@ typedef struct hough_server_config {
     int64_t slot_windows;  /* windows one batch can hold (>= 1)                         */
     int64_t slot_hits;     /* hits one batch can hold (>= 1)                            */
     int64_t max_queued;    /* requests waiting for a slot before submit says BUSY (>= 1) */
-    hough_launch launch;   /* launch shape of the server's batches; all 0: one CTA of
-                              1024 threads per SM with the largest tile (the lowest
-                              latency for small batches); the context's own shape is
-                              restored by hough_server_destroy */
+    hough_launch launch;   /* launch shape of the server's batches; all 0: chosen per
+                              batch, one CTA of 1024 threads per SM with 32-word-row
+                              tiles for batches of fewer than 2 windows per SM (the
+                              lowest latency), the context's shape when the server is
+                              created for larger ones (the library default, or what
+                              hough_set_launch or hough_autotune on representative
+                              windows chose: the highest throughput); the context's
+                              own shape is restored by hough_server_destroy */
 } hough_server_config;
 
 /*

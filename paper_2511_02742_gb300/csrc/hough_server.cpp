@@ -395,18 +395,13 @@ int hough_server_create(hough_ctx *ctx, const hough_server_config *cfg, hough_se
     // the server's launch shape: as given, else chosen per batch: one CTA of
     // 1024 threads per SM with 32-word-row tiles for small batches (they then
     // spread over every SM, and each window has the most warps), the
-    // context's default shape (several CTAs per SM, the highest throughput)
-    // for batches of at least two windows per SM
+    // context's own shape (the library default, or what hough_set_launch or
+    // hough_autotune chose for the workload) for batches of at least two
+    // windows per SM
     s->saved_launch = ctx->launch;
     hough_launch want = cfg->launch;
     if (want.threads == 0 && want.word_rows == 0 && want.hit_stage == 0 && want.ctas_per_sm == 0) {
-        const hough_launch def{}, lat{1024, 32, 2048, 1};
-        if (hough_set_launch(ctx, &def) != HOUGH_OK) {
-            ctx->launch = s->saved_launch;
-            delete s;
-            cudaSetDevice(prev);
-            return HOUGH_ERR_INVALID_ARG;
-        }
+        const hough_launch lat{1024, 32, 2048, 1};
         s->thr_launch = ctx->launch;
         want = lat;
         if (hough_set_launch(ctx, &want) != HOUGH_OK)
