@@ -69,15 +69,6 @@ __device__ void acc_vote_tile(const KParams &p, uint32_t *acc, const int2 *stage
 // with 4-byte stores, as does everything when the accumulator is not
 // 16-byte aligned or the tile has rows past n_theta (then row by row).
 template <int P>
-__device__ __forceinline__ int4 fields4(const uint4 &v, int s)
-{
-    constexpr int CW = 32 / P;
-    constexpr unsigned MASK = P == 1 ? 0xffffffffu : ((1u << CW) - 1u);
-    return make_int4((int)((v.x >> (s * CW)) & MASK), (int)((v.y >> (s * CW)) & MASK),
-                     (int)((v.z >> (s * CW)) & MASK), (int)((v.w >> (s * CW)) & MASK));
-}
-
-template <int P>
 __device__ void export_tile_rows(const KParams &p, uint32_t *acc, int t0, int R, long long w)
 {
     constexpr int CW = 32 / P;

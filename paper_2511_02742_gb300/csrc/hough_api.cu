@@ -61,12 +61,15 @@ static bool box_votes_in_range(const hough_geometry *g, int n_theta, int n_rho, 
 
 // Narrowed find tiles.  With WR word rows and P counters per word a tile
 // covers rows [k R, (k + 1) R), R = WR P.  Per WR, NB is the widest range of
-// reachable bins inside [0, n_rho) over every tile of every P (rounded up to
-// a multiple of 4), and tile k starts at lo = min(max(lowest reachable bin,
-// 0), n_rho - NB): [lo, lo + NB) then holds every reachable bin of the
-// tile's rows that lies in [0, n_rho), and lies in [0, n_rho) itself, so a
-// vote is inside [0, n_rho) exactly when it is inside the stored bins.  When
-// a bin below 0 is reachable, lo is 0.  lo_all: [WR index][log2 P][tile].
+// reachable bins inside [0, n_rho) over every tile of every P, plus 3,
+// rounded up to a multiple of 4 (at most n_rho), and tile k starts at
+// lo = min(max(lowest reachable bin, 0), n_rho - NB) rounded down to a
+// multiple of 4 (so that the export's 16-byte stores stay aligned; the 3
+// spare bins cover the rounding): [lo, lo + NB) then holds every reachable
+// bin of the tile's rows that lies in [0, n_rho), and lies in [0, n_rho)
+// itself, so a vote is inside [0, n_rho) exactly when it is inside the
+// stored bins.  When a bin below 0 is reachable, lo is 0.
+// lo_all: [WR index][log2 P][tile].
 static void narrow_tiles(hough_ctx *ctx, std::vector<int32_t> &lo_all)
 {
     const int nt = ctx->n_theta, nr = ctx->n_rho;
@@ -94,12 +97,12 @@ static void narrow_tiles(hough_ctx *ctx, std::vector<int32_t> &lo_all)
                     nb = std::max(nb, b - a + 1);
             }
         }
-        nb = std::min<long long>((nb + 3) & ~3LL, nr);
+        nb = std::min<long long>((nb + 3 + 3) & ~3LL, nr);
         ctx->tile_nb[wi] = (int)nb;
         for (int lp = 0; lp < 3; ++lp)
             for (int k = 0; k * (WR << lp) < nt; ++k)
-                lo_all[(size_t)(wi * 3 + lp) * stride + k] = (int32_t)std::min(
-                    std::max(tlo[(size_t)lp * stride + k], 0LL), (long long)nr - nb);
+                lo_all[(size_t)(wi * 3 + lp) * stride + k] = (int32_t)(std::min(
+                    std::max(tlo[(size_t)lp * stride + k], 0LL), (long long)nr - nb) & ~3LL);
     }
 }
 

@@ -784,51 +784,127 @@ __device__ void merge_peaks(const KParams &p, unsigned long long *keys,
     __syncthreads();
 }
 
-// Export mode: write the tile's rows as int32 to acc[w][t][b].  Lane = word
-// row (its own bank, so the loads are conflict-free): a warp takes 8 bins of
-// 32 word rows and writes each of the P rows of every word row as one whole
-// 32-byte sector (two 16-byte stores).  When the accumulator is not 16-byte
-// aligned the same values go out as plain 4-byte stores.
+// The P counters of four packed words as four int32 (field s of each).
 template <int P>
-__device__ void export_tile(const KParams &p, const uint32_t *acc, int t0, int R, int lo,
-                            long long w)
+__device__ __forceinline__ int4 fields4(const uint4 &v, int s)
 {
     constexpr int CW = 32 / P;
     constexpr unsigned MASK = P == 1 ? 0xffffffffu : ((1u << CW) - 1u);
-    const int WR = p.word_rows, G = WR >> 5;
+    return make_int4((int)((v.x >> (s * CW)) & MASK), (int)((v.y >> (s * CW)) & MASK),
+                     (int)((v.z >> (s * CW)) & MASK), (int)((v.w >> (s * CW)) & MASK));
+}
+
+// Export mode, at the end of a tile (after the check, when the tile is not
+// read again): the tile's rows written as int32 to acc[w][t][b], the carried
+// rows saved and the tile zeroed, with no barrier.  Each warp takes blocks of
+// 32 word rows x 32 stored bins (1024 consecutive words): it holds the block
+// in registers (saving its carried words, field P-1 of word rows WR-2 and
+// WR-1, when the block is in the last row group), writes it back transposed
+// in place -- word row r becomes 32 consecutive words, its 16-byte chunk c
+// stored at chunk c ^ (r & 7), so that the 16-byte writes and reads that
+// follow take the fewest wavefronts -- then each lane reads four bins of one
+// word row and writes each of its P theta rows with one 16-byte store (a warp
+// store covers four whole 128-byte lines), and the warp zeroes the block.
+// lo is a multiple of 4, so those stores are aligned.  Stored bins past the
+// last whole block, tiles with rows past n_theta and accumulators that are
+// not 16-byte aligned go out with 4-byte stores; the bins the tile does not
+// store are written as zeros.
+template <int P>
+__device__ void export_tile_end(const KParams &p, uint32_t *acc, int *carry0, int *carry1,
+                                bool save, int t0, int R, int lo, long long w)
+{
+    constexpr int CW = 32 / P;
+    constexpr unsigned MASK = P == 1 ? 0xffffffffu : ((1u << CW) - 1u);
+    const int WR = p.word_rows, G = WR >> 5, NB = p.n_b;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int nq = (p.n_rho + 7) >> 3;               // groups of 8 bins
+    const int nblk = NB >> 5;
     int32_t *out = p.acc + (size_t)w * p.n_theta * p.n_rho;
-    const bool vec = ((reinterpret_cast<uintptr_t>(p.acc) & 15u) == 0u);
-    for (int item = warp; item < G * nq; item += nw) {
-        const int g = item / nq, b0 = (item - g * nq) * 8;
-        const int wr = g * 32 + lane;
-        const int nb = min(8, p.n_rho - b0);            // 8, or 4 at a ragged end
-        const int j0 = b0 - lo;                         // bins outside [lo, lo + NB) are 0
-        uint32_t wv[8];
+    const bool vec = (reinterpret_cast<uintptr_t>(p.acc) & 15u) == 0u;
+    const bool fast = t0 + R <= p.n_theta && vec;
+    for (int item = warp; item < G * nblk; item += nw) {
+        const int g = item / nblk, j0 = (item - g * nblk) * 32;
+        uint32_t *blk = acc + (size_t)(g * NB + j0) * 32;
+        uint32_t r[32];
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-            wv[j] = (j < nb && (unsigned)(j0 + j) < (unsigned)p.n_b)
-                        ? acc[(size_t)(g * p.n_b + j0 + j) * 32 + lane] : 0u;
+        for (int j = 0; j < 32; ++j)
+            r[j] = blk[j * 32 + lane];                 // word (g*32 + lane, j0 + j)
+        if (save && g == G - 1 && lane >= 30) {
+            int *cr = lane == 30 ? carry0 : carry1;
 #pragma unroll
-        for (int s = 0; s < P; ++s) {
-            const int t = t0 + s * WR + wr;
-            if (s * WR + wr >= R || t >= p.n_theta)
-                continue;
-            int v[8];
+            for (int j = 0; j < 32; ++j)
+                cr[j0 + j] = field<P>(r[j], P - 1);
+        }
+        __syncwarp();
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-                v[j] = (int)((wv[j] >> (s * CW)) & MASK);
-            int32_t *row = out + (size_t)t * p.n_rho + b0;
+        for (int c = 0; c < 8; ++c)
+            *reinterpret_cast<uint4 *>(blk + lane * 32 + ((c ^ (lane & 7)) << 2)) =
+                make_uint4(r[4 * c], r[4 * c + 1], r[4 * c + 2], r[4 * c + 3]);
+        __syncwarp();
+        if (fast) {
+            // lane: word row q + (lane >> 3), bins lo + j0 + 4 (lane & 7) .. + 3
+            const int rs = lane >> 3, c = lane & 7;
+            int32_t *o = out + (size_t)(t0 + g * 32 + rs) * p.n_rho + lo + j0 + 4 * c;
+            const size_t sstep = (size_t)WR * p.n_rho;
+#pragma unroll 4
+            for (int q = 0; q < 32; q += 4) {
+                const int row = q + rs;
+                const uint4 v = *reinterpret_cast<const uint4 *>(blk + row * 32 + ((c ^ (row & 7)) << 2));
+#pragma unroll
+                for (int s = 0; s < P; ++s)
+                    *reinterpret_cast<int4 *>(o + (size_t)q * p.n_rho + s * sstep) = fields4<P>(v, s);
+            }
+        } else {
+            for (int q = 0; q < 32; ++q) {
+                const uint32_t v = blk[q * 32 + ((((lane >> 2) ^ (q & 7))) << 2) + (lane & 3)];
+#pragma unroll
+                for (int s = 0; s < P; ++s) {
+                    const int i = s * WR + g * 32 + q, t = t0 + i;
+                    if (i < R && t < p.n_theta)
+                        out[(size_t)t * p.n_rho + lo + j0 + lane] = (int)((v >> (s * CW)) & MASK);
+                }
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            *reinterpret_cast<uint4 *>(blk + lane * 32 + 4 * c) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    // stored bins past the last whole block: one lane per word row
+    const int rb = nblk * 32;
+    if (rb < NB) {
+        for (int g = warp; g < G; g += nw) {
+            const int wr = g * 32 + lane;
+            for (int j = rb; j < NB; ++j) {
+                const size_t idx = (size_t)(g * NB + j) * 32 + lane;
+                const uint32_t v = acc[idx];
+                if (save && g == G - 1 && lane >= 30)
+                    (lane == 30 ? carry0 : carry1)[j] = field<P>(v, P - 1);
+#pragma unroll
+                for (int s = 0; s < P; ++s) {
+                    const int i = s * WR + wr, t = t0 + i;
+                    if (i < R && t < p.n_theta)
+                        out[(size_t)t * p.n_rho + lo + j] = (int)((v >> (s * CW)) & MASK);
+                }
+                acc[idx] = 0u;
+            }
+        }
+    }
+    // the bins the tile does not store, [0, lo) and [lo + NB, n_rho) of every
+    // row: zeros, four bins per store (lo, NB and n_rho are multiples of 4)
+    const int nq = (p.n_rho - NB) >> 2;
+    if (nq > 0) {
+        const int nrows = min(R, p.n_theta - t0);
+        for (int x = threadIdx.x; x < nrows * nq; x += blockDim.x) {
+            const int i = x / nq, k = x - i * nq;
+            const int b = 4 * k < lo ? 4 * k : 4 * k + NB;
+            int32_t *o = out + (size_t)(t0 + i) * p.n_rho + b;
             if (vec) {
-                *reinterpret_cast<int4 *>(row) = make_int4(v[0], v[1], v[2], v[3]);
-                if (nb == 8)
-                    *reinterpret_cast<int4 *>(row + 4) = make_int4(v[4], v[5], v[6], v[7]);
+                *reinterpret_cast<int4 *>(o) = make_int4(0, 0, 0, 0);
             } else {
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    if (j < nb)
-                        row[j] = v[j];
+                o[0] = 0;
+                o[1] = 0;
+                o[2] = 0;
+                o[3] = 0;
             }
         }
     }
@@ -1038,8 +1114,6 @@ __device__ int process_tiles(const KParams &p, long long beg, int H, uint32_t *a
         // barrier: the votes are complete.  An overflow area that overflowed
         // sends the tile to the direct test of every counter.
         const bool lost = __syncthreads_or(lane == 0 && *ovf.count > p.seg_ovf);
-        if (p.export_acc)
-            export_tile<P>(p, acc, t0, R, lo, w);
         PeakSink ps{keys + p.kp + (size_t)warp * seg_cap, seg_cap, wc.n_pk[warp], 0, ws.kth,
                     ws.vk, vh + warp * kHistBins};
         if (!lost)
@@ -1052,7 +1126,10 @@ __device__ int process_tiles(const KParams &p, long long beg, int H, uint32_t *a
         }
         // every check step ended in a barrier, so neither the tile nor the
         // carried rows are read any more
-        tile_end<P>(p, acc, carry0, carry1, !last);
+        if (p.export_acc)
+            export_tile_end<P>(p, acc, carry0, carry1, !last, t0, R, lo, w);
+        else
+            tile_end<P>(p, acc, carry0, carry1, !last);
         lo_prev = lo;
         if (threadIdx.x < 32)
             wc.n_ovf[threadIdx.x] = 0;
