@@ -869,12 +869,14 @@ __device__ void export_tile_end(const KParams &p, uint32_t *acc, int *carry0, in
         for (int c = 0; c < 8; ++c)
             *reinterpret_cast<uint4 *>(blk + lane * 32 + 4 * c) = make_uint4(0u, 0u, 0u, 0u);
     }
-    // stored bins past the last whole block: one lane per word row
-    const int rb = nblk * 32;
-    if (rb < NB) {
-        for (int g = warp; g < G; g += nw) {
+    // stored bins past the last whole block: one bin of 32 word rows per warp
+    // step, one lane per word row
+    const int rb = nblk * 32, nr = NB - rb;
+    if (nr > 0) {
+        for (int x = warp; x < G * nr; x += nw) {
+            const int g = x / nr, j = rb + (x - g * nr);
             const int wr = g * 32 + lane;
-            for (int j = rb; j < NB; ++j) {
+            {
                 const size_t idx = (size_t)(g * NB + j) * 32 + lane;
                 const uint32_t v = acc[idx];
                 if (save && g == G - 1 && lane >= 30)
