@@ -166,7 +166,10 @@ typedef struct hough_tracks {
  * Launch shape of the find kernel; 0 in a field means "library default".
  * All fields 0: the first shape that fits of 3 CTAs of 256 threads per SM,
  * 2 of 512 and 1 of 1024, with 32-word-row tiles (else one CTA of 512
- * threads with the largest tile that fits).
+ * threads with the largest tile that fits); when that is 3 CTAs of 256
+ * threads, a batch of more than 200 hits per window on average runs in 2
+ * CTAs of 512 instead (its candidate lists need the larger CTAs' shared
+ * memory).  hough_get_launch returns the first choice.
  */
 typedef struct hough_launch {
     int32_t threads;      /* threads per CTA: 256, 512 or 1024                     */

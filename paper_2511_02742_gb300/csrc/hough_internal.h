@@ -29,6 +29,7 @@ struct hough_ctx {
     int32_t *d_C = nullptr, *d_S = nullptr;
     double *d_Cd = nullptr, *d_Sd = nullptr;   // cos/sin of the row centres (HOUGH_FLAG_FP64)
     hough_launch launch{};
+    bool auto_launch = true;   // the shape was left to the library (see launch_for)
     int num_sms = 0;
     size_t smem_optin = 0;
     size_t smem_per_sm = 0;
@@ -49,3 +50,8 @@ struct hough_ctx {
     int cf_K[2] = {0, 0};
     long long cf_D[2] = {0, 0};
 };
+
+// The find's launch shape for a batch (hough_api.cu): `base`, or a shape
+// chosen from the batch's mean hits per window when `automatic`.
+hough_launch launch_for(const hough_ctx *ctx, const hough_launch &base, bool automatic,
+                        int64_t n_hits, int64_t n_windows);

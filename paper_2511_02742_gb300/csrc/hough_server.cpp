@@ -112,6 +112,8 @@ struct hough_server {
     // context's default (throughput) shape
     bool per_batch = false;
     hough_launch lat_launch{}, thr_launch{};
+    bool thr_auto = false;           // thr_launch was left to the library
+    bool saved_auto = false;         // the context's flag before the server
     int max_peaks = 0;
     size_t in_cap = 0, out_cap = 0, stage_cap = 0;
     std::vector<Slot> slots;
@@ -190,7 +192,9 @@ int launch_slot(hough_server *s, Slot &sl)
     t.hit_track = reinterpret_cast<int32_t *>(sl.d_out + O.ht);
     t.track_hits = reinterpret_cast<int32_t *>(sl.d_out + O.th);
     if (s->per_batch)
-        s->ctx->launch = sl.W >= 2 * (int64_t)s->ctx->num_sms ? s->thr_launch : s->lat_launch;
+        s->ctx->launch = sl.W >= 2 * (int64_t)s->ctx->num_sms
+                             ? launch_for(s->ctx, s->thr_launch, s->thr_auto, sl.H, sl.W)
+                             : s->lat_launch;
     int rc = hough_find(s->ctx, &hits, reinterpret_cast<const int64_t *>(sl.d_in + L.off), sl.W,
                         &t, sl.stream);
     if (rc != HOUGH_OK)
@@ -399,6 +403,8 @@ int hough_server_create(hough_ctx *ctx, const hough_server_config *cfg, hough_se
     // hough_autotune chose for the workload) for batches of at least two
     // windows per SM
     s->saved_launch = ctx->launch;
+    s->saved_auto = ctx->auto_launch;
+    s->thr_auto = ctx->auto_launch;
     hough_launch want = cfg->launch;
     if (want.threads == 0 && want.word_rows == 0 && want.hit_stage == 0 && want.ctas_per_sm == 0) {
         const hough_launch lat{1024, 32, 2048, 1};
@@ -412,6 +418,7 @@ int hough_server_create(hough_ctx *ctx, const hough_server_config *cfg, hough_se
     }
     if (hough_set_launch(ctx, &want) != HOUGH_OK) {
         ctx->launch = s->saved_launch;
+        ctx->auto_launch = s->saved_auto;
         delete s;
         cudaSetDevice(prev);
         return HOUGH_ERR_INVALID_ARG;
@@ -452,6 +459,7 @@ int hough_server_create(hough_ctx *ctx, const hough_server_config *cfg, hough_se
         cudaGetLastError();
         free_slots(s);
         ctx->launch = s->saved_launch;
+        ctx->auto_launch = s->saved_auto;
         delete s;
         cudaSetDevice(prev);
         return rc;
@@ -462,6 +470,7 @@ int hough_server_create(hough_ctx *ctx, const hough_server_config *cfg, hough_se
     } catch (...) {
         free_slots(s);
         ctx->launch = s->saved_launch;
+        ctx->auto_launch = s->saved_auto;
         delete s;
         cudaSetDevice(prev);
         return HOUGH_ERR_ALLOC;
@@ -593,6 +602,7 @@ void hough_server_destroy(hough_server *s)
     cudaSetDevice(s->ctx->device);
     free_slots(s);
     s->ctx->launch = s->saved_launch;
+    s->ctx->auto_launch = s->saved_auto;
     cudaSetDevice(prev);
     delete s;
 }

@@ -229,10 +229,12 @@ def test_pageable_request_buffers():
     f.close()
 
 
-def test_small_and_large_batches_under_the_default_shapes():
+@pytest.mark.parametrize("tuned", [True, False])
+def test_small_and_large_batches_under_the_default_shapes(tuned):
     """With the launch shape left open the server runs a batch of fewer than
     two windows per SM with one 1024-thread CTA per SM and a larger one with
-    the context's default shape; both give the bits hough_find gives, and the
+    the context's shape (set, or left to the library, which picks it from the
+    batch's hits per window); all give the bits hough_find gives, and the
     context's own shape is back after the server is closed."""
     import torch
     from paper_2511_02742_gb300 import hough
@@ -240,7 +242,8 @@ def test_small_and_large_batches_under_the_default_shapes():
     cfg = synth.WORKLOADS["serving"]
     w = synth.workload("serving", n_windows=4 * sms + 200, seed=12)
     f = hough.Finder(cfg["n_theta"], cfg["n_rho"])
-    hough.hough_set_launch(f.ctx, 512, 32, 1024, 2)
+    if tuned:
+        hough.hough_set_launch(f.ctx, 512, 32, 1024, 2)
     before = hough.hough_get_launch(f.ctx)
     ref = _reference(hough, f, w)
     srv = hough.Server(f, n_slots=2, slot_windows=4 * sms + 200, slot_hits=1 << 21)
