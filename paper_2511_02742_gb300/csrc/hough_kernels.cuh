@@ -427,9 +427,36 @@ struct TileView {
         const int i = t - t0, j = b - lo;
         if (i >= 1 && i + 1 < R && t + 1 < n_theta && j >= 1 && j + 1 < n_b)
             return is_peak_inside(i, j, v);
+        const int jc = b - lo_prev;
+        if (t0 > 0 && (i == 0 || i == -1) && t + 1 < n_theta && j >= 1 && j + 1 < n_b &&
+            jc >= 1 && jc + 1 < n_b)
+            return is_peak_carried(i, j, jc, v);
         const int a0 = get(t - 1, b - 1), a1 = get(t - 1, b), a2 = get(t - 1, b + 1);
         const int a3 = get(t, b - 1), a4 = get(t, b + 1);
         const int a5 = get(t + 1, b - 1), a6 = get(t + 1, b), a7 = get(t + 1, b + 1);
+        const int earlier = max(max(a0, a1), max(a2, a3));
+        const int later = max(max(a4, a5), max(a6, a7));
+        return v > earlier && v >= later;
+    }
+
+    // The rule for tile row 0 (i = 0) and the carried row (i = -1) of a tile
+    // that has a previous one, when the bin's neighbours lie in the stored
+    // bins of both tiles (j in this tile, jc in the previous one): the rows
+    // above come from the carried rows, the rest from the tile, with plain
+    // loads.
+    __device__ __forceinline__ bool is_peak_carried(int i, int j, int jc, int v) const
+    {
+        constexpr unsigned MASK = P == 1 ? 0xffffffffu : ((1u << (32 / P)) - 1u);
+        const int *up = i == 0 ? carry1 : carry0;           // row i - 1
+        const int a0 = up[jc - 1], a1 = up[jc], a2 = up[jc + 1];
+        int sb, sc;
+        const int wb = row_word(0, j, sb);                  // tile row 0
+        const int wc = row_word(i + 1, j, sc);              // row i + 1, in the tile
+        const int t3 = (int)((acc[wb - 32] >> sb) & MASK), t4 = (int)((acc[wb + 32] >> sb) & MASK);
+        const int c3 = carry1[jc - 1], c4 = carry1[jc + 1];
+        const int a3 = i == 0 ? t3 : c3, a4 = i == 0 ? t4 : c4;   // row i itself
+        const int a5 = (int)((acc[wc - 32] >> sc) & MASK), a6 = (int)((acc[wc] >> sc) & MASK);
+        const int a7 = (int)((acc[wc + 32] >> sc) & MASK);
         const int earlier = max(max(a0, a1), max(a2, a3));
         const int later = max(max(a4, a5), max(a6, a7));
         return v > earlier && v >= later;
