@@ -699,16 +699,23 @@ def _flush_l2(buf):
     buf.add_(1)
 
 
+def find_kernel_source_sha256():
+    """sha256 of the find kernel's source: hough_kernels.cuh, then hough_find.cu."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("hough_kernels.cuh", "hough_find.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2511_02742_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()
+
+
 def _recorded_traffic(workload, n_windows):
     """DRAM bytes per launch of find_kernel from the committed ncu summary, if
     that capture was of the kernel source as it is now (else None)."""
-    import hashlib
     p = os.path.join(ROOT, "profiles", "find_kernel_batched.traffic.json")
-    src = os.path.join(ROOT, "paper_2511_02742_gb300", "csrc", "hough_kernels.cuh")
     if workload != "batched" or not os.path.exists(p):
         return None, "no capture of this workload"
     d = json.load(open(p))
-    if d.get("kernel_source_sha256") != hashlib.sha256(open(src, "rb").read()).hexdigest():
+    if d.get("kernel_source_sha256") != find_kernel_source_sha256():
         return None, "kernel changed since the capture"
     scaled = d["measured_dram_bytes"] * n_windows / d["measured_windows"]
     return int(round(scaled)), (f"ncu dram__bytes_read+write on {d['measured_windows']} windows, "

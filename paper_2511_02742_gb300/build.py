@@ -1,9 +1,10 @@
 """Build libhough.so (the CUDA path) in-tree with nvcc for sm_103a.
 
-The library is two translation units -- the C ABI with the kernels
-(hough_api.cu) and the host-only request loop (hough_server.cpp) -- linked
-against the static CUDA runtime so that the shared object only needs the
-driver.
+The library is four translation units, compiled in parallel: the C ABI with
+the other kernels (hough_api.cu), the fixed-point find kernels
+(hough_find.cu), the FP64 variant's find kernel (hough_find_fp64.cu) and the
+host-only request loop (hough_server.cpp); they are linked against the static
+CUDA runtime so that the shared object only needs the driver.
 """
 from __future__ import annotations
 
@@ -16,7 +17,10 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 SRC = os.path.join(PKG, "csrc", "hough_api.cu")
 SERVER_SRC = os.path.join(PKG, "csrc", "hough_server.cpp")
-DEPS = [SRC, SERVER_SRC, os.path.join(PKG, "csrc", "hough_kernels.cuh"),
+FIND_SRCS = [os.path.join(PKG, "csrc", "hough_find.cu"), os.path.join(PKG, "csrc", "hough_find_fp64.cu")]
+UNITS = [SRC, *FIND_SRCS, SERVER_SRC]
+DEPS = [*UNITS, os.path.join(PKG, "csrc", "hough_kernels.cuh"),
+        os.path.join(PKG, "csrc", "hough_encode.cuh"),
         os.path.join(PKG, "csrc", "hough_internal.h"), os.path.join(PKG, "csrc", "hough_coarse_fine.cuh"),
         os.path.join(PKG, "csrc", "hough_iterative.cuh"),
         os.path.join(PKG, "csrc", "hough_extend.cuh"),
@@ -45,19 +49,38 @@ def needs_build() -> bool:
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if not force and not needs_build():
         return LIB
+    from concurrent.futures import ThreadPoolExecutor
     os.makedirs(OUT_DIR, exist_ok=True)
-    tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc(), ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-pthread",
-           "-shared", "-I", os.path.join(ROOT, "include"), "-o", tmp, SRC, SERVER_SRC, *extra]
+    tag = f".{os.getpid()}"
+    objs = [os.path.join(OUT_DIR, os.path.basename(u) + tag + ".o") for u in UNITS]
+    flags = [ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-pthread",
+             "-I", os.path.join(ROOT, "include"), *extra]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    res = subprocess.run(cmd, capture_output=True, text=True)
-    if res.returncode != 0:
-        sys.stderr.write(res.stdout + res.stderr)
-        raise RuntimeError("nvcc failed building libhough")
-    if verbose:
-        sys.stderr.write(res.stdout + res.stderr)
-    os.replace(tmp, LIB)
+        flags.insert(0, "-Xptxas=-v")
+
+    def compile_unit(k):
+        return subprocess.run([nvcc(), *flags, "-c", "-o", objs[k], UNITS[k]],
+                              capture_output=True, text=True)
+
+    try:
+        with ThreadPoolExecutor(len(UNITS)) as ex:
+            results = list(ex.map(compile_unit, range(len(UNITS))))
+        for res in results:
+            if verbose or res.returncode != 0:
+                sys.stderr.write(res.stdout + res.stderr)
+        if any(res.returncode != 0 for res in results):
+            raise RuntimeError("nvcc failed building libhough")
+        tmp = LIB + tag + ".tmp"
+        res = subprocess.run([nvcc(), ARCH, "-shared", "-Xcompiler", "-pthread", "-o", tmp, *objs],
+                             capture_output=True, text=True)
+        if res.returncode != 0:
+            sys.stderr.write(res.stdout + res.stderr)
+            raise RuntimeError("nvcc failed linking libhough")
+        os.replace(tmp, LIB)
+    finally:
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
     return LIB
 
 

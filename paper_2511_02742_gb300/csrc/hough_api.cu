@@ -25,6 +25,7 @@
 #include "hough_extend.cuh"
 #include "hough_slice.cuh"
 #include "hough_accumulate.cuh"
+#include "hough_encode.cuh"
 
 // The lowest and highest bin that a hit of the detector box can vote in row
 // t: the bin is monotone in phi and in z, so the box's four corners bound it
@@ -424,8 +425,8 @@ using FindKernel = void (*)(hk::KParams);
 static FindKernel find_kernel_of(const hough_ctx *ctx, int threads)
 {
     if (ctx->th.flags & HOUGH_FLAG_FP64)
-        return hk::find_kernel<true>;
-    return threads <= 256 ? hk::find_kernel_256 : hk::find_kernel<false>;
+        return hk::find_kernel_fp64;
+    return threads <= 256 ? hk::find_kernel_256 : hk::find_kernel;
 }
 
 // Resolve a launch shape, raise the kernel's shared-memory limit and size the

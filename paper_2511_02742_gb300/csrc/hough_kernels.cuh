@@ -218,8 +218,8 @@ __device__ __forceinline__ unsigned atom_add_shared(unsigned addr, unsigned v)
 
 // Stage hits [base, base + n) of the global arrays into `stage`, keeping only
 // valid hits, in their original order.  Returns the number staged (uniform).
-__device__ int stage_hits(const KParams &p, long long base, int n, int2 *stage, int *wtot,
-                          WinScalars &ws)
+__device__ inline int stage_hits(const KParams &p, long long base, int n, int2 *stage, int *wtot,
+                                 WinScalars &ws)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     int total = 0;
@@ -661,9 +661,9 @@ __device__ __forceinline__ void decode_entry(const KParams &p, const TileView<P>
 //     is the number of smaller keys (keys are distinct), so the best max_peaks
 //     are written in order to a staging area and then to keys[0 ..).
 // kth is tightened and the segments are emptied.
-__device__ void merge_peaks(const KParams &p, unsigned long long *keys,
-                            unsigned long long *top_stage, int seg_cap, WarpCounters wc,
-                            const int *hist, WinScalars &ws)
+__device__ inline void merge_peaks(const KParams &p, unsigned long long *keys,
+                                   unsigned long long *top_stage, int seg_cap, WarpCounters wc,
+                                   const int *hist, WinScalars &ws)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const unsigned lt = lanemask_lt();
@@ -1524,32 +1524,13 @@ __device__ __forceinline__ void find_body(const KParams &p)
     }
 }
 
-// Any CTA size up to 1024 threads (64 registers a thread).
-template <bool F64>
-__global__ void __launch_bounds__(1024, 1) find_kernel(KParams p)
-{
-    find_body<F64>(p);
-}
-
-// Fixed point, CTAs of at most 256 threads, three per SM: up to 80 registers
-// a thread instead of 64, so that the vote loop and the candidate test keep
-// their operands in registers (6% faster on the batched pileup windows).
-__global__ void __launch_bounds__(256, 3) find_kernel_256(KParams p)
-{
-    find_body<false>(p);
-}
-
-// Step A alone: strip addresses -> fixed-point (phi, z).
-__global__ void encode_kernel(const int32_t *vane, const int32_t *strip, long long n, int vane_step,
-                              int z_min_u, int z_pitch_u, int z_half, int32_t *phi_q, int32_t *z_q)
-{
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        phi_q[i] = (int32_t)((long long)vane_step * (long long)__ldg(vane + i));
-        z_q[i] = (int32_t)((long long)z_min_u + (long long)z_pitch_u * (long long)__ldg(strip + i) +
-                           z_half);
-    }
-}
-
+// The find kernels (instances of find_body), compiled in translation units of
+// their own so that they build in parallel: find_kernel (fixed point, any CTA
+// size up to 1024 threads) and find_kernel_256 (fixed point, CTAs of at most
+// 256 threads) in hough_find.cu, find_kernel_fp64 (HOUGH_FLAG_FP64) in
+// hough_find_fp64.cu.
+__global__ void find_kernel(KParams p);
+__global__ void find_kernel_256(KParams p);
+__global__ void find_kernel_fp64(KParams p);
 
 }  // namespace hk
