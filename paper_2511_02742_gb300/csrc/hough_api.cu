@@ -972,7 +972,8 @@ int hough_find_iterative(hough_ctx *ctx, const hough_hits *hits, const int64_t *
         return fail(ctx, HOUGH_ERR_CUDA);
     const size_t room = ctx->smem_optin + 128 > fa.sharedSizeBytes
                             ? ctx->smem_optin + 128 - fa.sharedSizeBytes : 0;
-    const size_t smem = (size_t)l.word_rows * ctx->n_rho * 4 + stage;
+    // the find's narrowed tiles
+    const size_t smem = (size_t)l.word_rows * tile_bins(ctx, l.word_rows) * 4 + stage;
     if (smem > room)
         return fail(ctx, HOUGH_ERR_UNSUPPORTED_SHAPE);
     if (raise_smem_limit(reinterpret_cast<const void *>(hk::iterative_kernel), smem) != HOUGH_OK)
@@ -981,7 +982,7 @@ int hough_find_iterative(hough_ctx *ctx, const hough_hits *hits, const int64_t *
     out.hit_track = hit_track;
     out.window_status = window_status;
     hk::IterParams q{};
-    q.k = make_params(ctx, hits, window_offsets, n_windows, &out, nullptr, l, false);
+    q.k = make_params(ctx, hits, window_offsets, n_windows, &out, nullptr, l);
     q.max_tracks = max_tracks;
     q.tracks = reinterpret_cast<int4 *>(tracks);
     q.n_tracks = n_tracks;

@@ -6,9 +6,10 @@
 //
 // One CTA per window (grid-stride).  The window's valid hits are staged in
 // shared memory with their window-local indices; every iteration runs the
-// theta tiles of the find kernel's vote loop (vote_tile, with candidate
-// listing switched off) and a block maximum over each tile's counters, then
-// marks the line's hits and compacts them out of the stage in order.
+// theta tiles of the find kernel's vote loop (its narrowed tiles, vote_tile
+// with candidate listing switched off) and a block maximum over each tile's
+// counters, then marks the line's hits and compacts them out of the stage in
+// order.
 #pragma once
 
 #include "hough_kernels.cuh"
@@ -103,12 +104,12 @@ __device__ __forceinline__ bool has_field(uint32_t w, unsigned v)
 // vote, so every non-zero field is a bin of the accumulator), then the words
 // holding that count.  Every thread gets the result.
 template <int P>
-__device__ unsigned long long tile_best(const KParams &p, const uint32_t *acc, int t0,
+__device__ unsigned long long tile_best(const KParams &p, const uint32_t *acc, int t0, int lo,
                                         unsigned long long *red)
 {
     constexpr int CW = 32 / P;
     constexpr unsigned MASK = P == 1 ? 0xffffffffu : ((1u << CW) - 1u);
-    const int words = p.word_rows * p.n_rho;
+    const int words = p.word_rows * p.n_b;
     unsigned m = 0u;
     for (int f = threadIdx.x; f < words; f += blockDim.x) {
         const uint32_t wv = acc[f];
@@ -125,8 +126,8 @@ __device__ unsigned long long tile_best(const KParams &p, const uint32_t *acc, i
         if (!has_field<P>(wv, top))
             continue;
         const int q = f >> 5;
-        const int g = (int)__umulhi((unsigned)q, p.nrho_inv);
-        const int b = q - g * p.n_rho;
+        const int g = (int)__umulhi((unsigned)q, p.nb_inv);
+        const int b = q - g * p.n_b + lo;                   // the tile stores bins lo ..
         const int wr = g * 32 + (f & 31);
 #pragma unroll
         for (int s = 0; s < P; ++s) {
@@ -159,6 +160,8 @@ __device__ unsigned long long iter_best(const KParams &p, uint32_t *acc, const i
     const int R = p.word_rows * P;
     const int n_tiles = (p.n_theta + R - 1) / R;
     const int lane = threadIdx.x & 31;
+    constexpr int lgP = P == 4 ? 2 : (P == 2 ? 1 : 0);
+    const int32_t *lo_row = p.lo_tab ? p.lo_tab + lgP * p.lo_stride : nullptr;
     unsigned long long best = 0ull;
     int best_tile = n_tiles;
     int cnt = 0;
@@ -189,16 +192,17 @@ __device__ unsigned long long iter_best(const KParams &p, uint32_t *acc, const i
         if ((int)bound < T || bound < top || (bound == top && tile > best_tile))
             break;                                   // no unvisited tile can hold the highest bin
         const int t0 = tile * R;
+        const int lo = lo_row ? __ldg(lo_row + tile) : 0;
         uint4 *acc4 = reinterpret_cast<uint4 *>(acc);
-        for (int i = threadIdx.x; i < (p.word_rows * p.n_rho) >> 2; i += blockDim.x)
+        for (int i = threadIdx.x; i < (p.word_rows * p.n_b) >> 2; i += blockDim.x)
             acc4[i] = make_uint4(0u, 0u, 0u, 0u);
         __syncthreads();
         if (p.in_range && t0 + R <= p.n_theta)
-            vote_tile<P, true>(p, acc, stage, nv, t0, 0, nullptr, 0, cnt, none, ws);
+            vote_tile<P, true>(p, acc, stage, nv, t0, lo, nullptr, 0, cnt, none, ws);
         else
-            vote_tile<P, false>(p, acc, stage, nv, t0, 0, nullptr, 0, cnt, none, ws);
+            vote_tile<P, false>(p, acc, stage, nv, t0, lo, nullptr, 0, cnt, none, ws);
         __syncthreads();
-        const unsigned long long k = tile_best<P>(p, acc, t0, red);
+        const unsigned long long k = tile_best<P>(p, acc, t0, lo, red);
         if (threadIdx.x == 0) {
             ub[tile] = (int)(k >> 32);
             done[tile >> 5] |= 1u << (tile & 31);
@@ -225,7 +229,7 @@ __global__ void __launch_bounds__(512, 1) iterative_kernel(IterParams q)
     p.T = 0x7fffffff;               // the vote loop lists nothing
     const int T = q.k.T;
     uint32_t *acc = reinterpret_cast<uint32_t *>(smem);
-    int2 *stage = reinterpret_cast<int2 *>(smem + (size_t)p.word_rows * p.n_rho * 4);
+    int2 *stage = reinterpret_cast<int2 *>(smem + (size_t)p.word_rows * p.n_b * 4);
     int *sidx = reinterpret_cast<int *>(stage + p.hit_stage);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (long long w = blockIdx.x; w < p.n_windows; w += gridDim.x) {
