@@ -20,10 +20,10 @@
 // exact.  A tile stores only NB bins [lo, lo + NB) of each row: the bin is
 // monotone in phi and in z, so the corners of the detector box bound the bins
 // that any hit can reach in a row, and the host gives every tile the first
-// bin lo (a multiple of 4) of a window of NB bins that holds every reachable
-// bin inside [0, n_rho) of its rows (NB = 304 of 512 bins for 128-row tiles
-// at 512 x 512, 592 of 1024 at 1024 x 1024; NB = n_rho, lo = 0 when no table
-// is given).  Bins outside the window are zero in that tile.  Words are stored bank-private: word (wr, j) lives at
+// bin lo of a window of NB bins that holds every reachable bin inside
+// [0, n_rho) of its rows (NB about 0.6 n_rho for 128-row tiles over half a
+// turn; NB = n_rho, lo = 0 when no table is given).  Bins outside the window
+// are zero in that tile.  Words are stored bank-private: word (wr, j) lives at
 //     ((wr / 32) * NB + j) * 32 + wr % 32,
 // so every word of word row wr sits in shared-memory bank wr % 32.
 //
