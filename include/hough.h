@@ -167,7 +167,7 @@ typedef struct hough_tracks {
  * All fields 0: the first shape that fits of 3 CTAs of 256 threads per SM,
  * 2 of 512 and 1 of 1024, with 32-word-row tiles (else one CTA of 512
  * threads with the largest tile that fits); when that is 3 CTAs of 256
- * threads, a batch of more than 200 hits per window on average runs in 2
+ * threads, a batch of more than 250 hits per window on average runs in 2
  * CTAs of 512 instead (its candidate lists need the larger CTAs' shared
  * memory).  hough_get_launch returns the first choice.
  */

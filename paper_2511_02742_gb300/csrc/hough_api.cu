@@ -301,10 +301,13 @@ int resolve_launch(const hough_ctx *ctx, const hough_launch &in, hough_launch &o
 // when the shape was left to the library (automatic) and its default is
 // three 256-thread CTAs per SM, two 512-thread CTAs per SM for windows of
 // more than kHeavyWindowHits hits on average.  Heavier windows list more
-// candidate bins per tile than the small CTAs' shared memory holds (windows
-// of ~300 hits, half of them past the 8-bit limit: two 512-thread CTAs 19%
-// faster; windows of ~140 hits: three 256-thread CTAs 25% faster).
-constexpr int64_t kHeavyWindowHits = 200;
+// candidate bins per tile than the small CTAs' shared memory holds.  Where
+// the shapes cross depends on the spread of window sizes as well as the
+// mean: Poisson mixes of tracks at 71 / 143 / 199 / 256 / 313 / 427 hits per
+// window ran 0.71 / 0.78 / 0.83 / 0.87 / 0.99 / 1.16 times as long in three
+// 256-thread CTAs as in two 512-thread ones, and a uniform mix of 1 to 40
+// tracks (295 hits, with a long tail) 1.24 times.
+constexpr int64_t kHeavyWindowHits = 250;
 
 }  // namespace
 
