@@ -199,6 +199,27 @@ int hough_tables(const hough_geometry *g, int n_theta, int n_rho, int32_t *C, in
                  int64_t *D, int32_t *K);
 
 /*
+ * The find's narrowed tiles, host only (no GPU).  The bin of Eq. (1) is
+ * monotone in phi and in z, so in each theta row the bins a hit of the
+ * detector box can reach lie between those of the box's four corners.  A
+ * find tile with word_rows (32, 64 or 128) word rows and 2^k counters per
+ * word (k = 0, 1, 2: 32-, 16-, 8-bit counters) covers theta rows
+ * [i R, (i + 1) R), R = word_rows << k, and stores only the bins
+ * [lo, lo + *nb) of each row: *nb is the widest range of reachable bins
+ * inside [0, n_rho) over every such tile, plus 3, rounded up to a multiple
+ * of 4 (at most n_rho), and lo = min(max(lowest reachable bin of the tile,
+ * 0), n_rho - *nb) rounded down to a multiple of 4.  lo[k * T + i] (caller's
+ * array of 3 T entries, T = ceil(n_theta / 32); entries past a width's last
+ * tile are 0) receives tile i's first bin for counter width 2^k.  Contexts
+ * use these for the fixed-point find (not for HOUGH_FLAG_FP64 or
+ * hough_find_noalloc, whose tiles store every bin).
+ * Errors: INVALID_ARG (null pointer, bad geometry or word_rows),
+ * UNSUPPORTED_SHAPE (as hough_create).
+ */
+int hough_tile_bins(const hough_geometry *g, int n_theta, int n_rho, int word_rows, int32_t *nb,
+                    int32_t *lo);
+
+/*
  * Create a context on the current CUDA device for one accumulator shape
  * (Section 5: 180 x 1000 in the paper; any 1 <= n_theta <= HOUGH_MAX_THETA,
  * 4 <= n_rho <= HOUGH_MAX_RHO with n_rho % 4 == 0).  Copies g and th, builds

@@ -70,15 +70,16 @@ static bool box_votes_in_range(const hough_geometry *g, int n_theta, int n_rho, 
 // bin of the tile's rows that lies in [0, n_rho), and lies in [0, n_rho)
 // itself, so a vote is inside [0, n_rho) exactly when it is inside the
 // stored bins.  When a bin below 0 is reachable, lo is 0.
-// lo_all: [WR index][log2 P][tile].
-static void narrow_tiles(hough_ctx *ctx, std::vector<int32_t> &lo_all)
+// nb[WR index]; lo_all: [WR index][log2 P][tile], tiles ceil(n_theta / 32)
+// apart.
+static void narrow_tiles(const hough_geometry *g, int nt, int nr, const int32_t *C,
+                         const int32_t *S, long long D, int K, int nb_out[3],
+                         std::vector<int32_t> &lo_all)
 {
-    const int nt = ctx->n_theta, nr = ctx->n_rho;
     std::vector<long long> rlo(nt), rhi(nt);
     for (int t = 0; t < nt; ++t)
-        row_reach(&ctx->g, ctx->C.data(), ctx->S.data(), ctx->D, ctx->K, t, rlo[t], rhi[t]);
+        row_reach(g, C, S, D, K, t, rlo[t], rhi[t]);
     const int stride = (nt + 31) / 32;
-    ctx->lo_stride = stride;
     lo_all.assign((size_t)9 * stride, 0);
     for (int wi = 0; wi < 3; ++wi) {
         const int WR = 32 << wi;
@@ -99,7 +100,7 @@ static void narrow_tiles(hough_ctx *ctx, std::vector<int32_t> &lo_all)
             }
         }
         nb = std::min<long long>((nb + 3 + 3) & ~3LL, nr);
-        ctx->tile_nb[wi] = (int)nb;
+        nb_out[wi] = (int)nb;
         for (int lp = 0; lp < 3; ++lp)
             for (int k = 0; k * (WR << lp) < nt; ++k)
                 lo_all[(size_t)(wi * 3 + lp) * stride + k] = (int32_t)(std::min(
@@ -548,6 +549,29 @@ int hough_tables(const hough_geometry *g, int n_theta, int n_rho, int32_t *C, in
     return HOUGH_ERR_UNSUPPORTED_SHAPE;
 }
 
+int hough_tile_bins(const hough_geometry *g, int n_theta, int n_rho, int word_rows, int32_t *nb,
+                    int32_t *lo)
+{
+    if (!geometry_ok(g) || !nb || !lo || !(word_rows == 32 || word_rows == 64 || word_rows == 128))
+        return HOUGH_ERR_INVALID_ARG;
+    if (n_theta < 1 || n_theta > HOUGH_MAX_THETA || n_rho < 4 || n_rho > HOUGH_MAX_RHO ||
+        n_rho % 4 != 0)
+        return HOUGH_ERR_UNSUPPORTED_SHAPE;
+    std::vector<int32_t> C(n_theta), S(n_theta), lo_all;
+    int64_t D = 0;
+    int32_t K = 0;
+    const int rc = hough_tables(g, n_theta, n_rho, C.data(), S.data(), &D, &K);
+    if (rc != HOUGH_OK)
+        return rc;
+    int nbs[3];
+    narrow_tiles(g, n_theta, n_rho, C.data(), S.data(), D, K, nbs, lo_all);
+    const int wi = word_rows == 32 ? 0 : (word_rows == 64 ? 1 : 2);
+    const size_t per = (size_t)3 * ((n_theta + 31) / 32);
+    *nb = nbs[wi];
+    std::memcpy(lo, lo_all.data() + (size_t)wi * per, per * sizeof(int32_t));
+    return HOUGH_OK;
+}
+
 int hough_create(const hough_geometry *g, int n_theta, int n_rho, const hough_thresholds *th,
                  hough_ctx **out)
 {
@@ -607,7 +631,9 @@ int hough_create(const hough_geometry *g, int n_theta, int n_rho, const hough_th
         // narrowed tiles (the FP64 variant's bins come from another formula,
         // so its tiles keep every bin)
         std::vector<int32_t> lo_all;
-        narrow_tiles(ctx, lo_all);
+        narrow_tiles(&ctx->g, ctx->n_theta, ctx->n_rho, ctx->C.data(), ctx->S.data(), ctx->D,
+                     ctx->K, ctx->tile_nb, lo_all);
+        ctx->lo_stride = (ctx->n_theta + 31) / 32;
         if (cudaMalloc(&ctx->d_lo, sizeof(int32_t) * lo_all.size()) != cudaSuccess) {
             hough_destroy(ctx);
             return HOUGH_ERR_ALLOC;

@@ -134,6 +134,7 @@ def load(build_if_missing: bool = False):
     i32, i64 = ctypes.c_int, ctypes.c_int64
     sig = {
         "hough_tables": ([P, i32, i32, P, P, P, P], i32),
+        "hough_tile_bins": ([P, i32, i32, i32, P, P], i32),
         "hough_create": ([P, i32, i32, P, P], i32),
         "hough_destroy": ([P], None),
         "hough_encode": ([P, P, P, i64, P, P, P], i32),
@@ -220,6 +221,18 @@ def hough_tables(geometry: dict, n_theta: int, n_rho: int):
     _check(lib.hough_tables(ctypes.byref(g), n_theta, n_rho, _ptr(C), _ptr(S), _ptr(D), _ptr(K)),
            "hough_tables")
     return C, S, int(D[0]), int(K[0])
+
+
+def hough_tile_bins(geometry: dict, n_theta: int, n_rho: int, word_rows: int):
+    """Host-only narrowed-tile layout of the find: (NB, lo int32[3, ceil(n_theta/32)]),
+    lo[k, i] the first stored bin of tile i with 2^k counters per word."""
+    lib = load()
+    g = make_geometry(geometry)
+    nb = np.zeros(1, np.int32)
+    lo = np.zeros(3 * ((n_theta + 31) // 32), np.int32)
+    _check(lib.hough_tile_bins(ctypes.byref(g), n_theta, n_rho, word_rows, _ptr(nb), _ptr(lo)),
+           "hough_tile_bins")
+    return int(nb[0]), lo.reshape(3, -1)
 
 
 def hough_create(geometry: dict, n_theta: int, n_rho: int, vote_threshold=5, assoc_tol_bins=1,
